@@ -1,0 +1,191 @@
+/*
+ * bc.h — C ABI of the GB300 exact betweenness-centrality library (libbc.so).
+ *
+ * Method: Vella, Carbone, Bernaschi, "Algorithms and Heuristics for Scalable
+ * Betweenness Centrality Computation on Multi-GPU Systems" (arXiv 1602.00963).
+ *   BC(v)      = sum_{s != v != t} sigma_st(v) / sigma_st                      (Eq. 1)
+ *   delta_s(v) = sum_{w : v in pred(w)} sigma_sv / sigma_sw * (1 + delta_s(w)) (Eq. 2)
+ *   BC(v)      = sum_{s != v} delta_s(v)                                       (Eq. 3)
+ * computed per source by a level-synchronous BFS that counts sigma (Alg. 2, 3) and a
+ * backward sweep over the same levels (Alg. 4, 5); optionally with the 1-degree
+ * reduction of Eq. 3 / Eq. 4 and Alg. 6 (Sec. 3.4.1).
+ *
+ * Conventions (all entry points):
+ *   - Graphs are undirected and unweighted, given as a symmetric CSR with int32 indices:
+ *     row_ptr[n+1], col_idx[nnz], each unordered edge present in both rows, rows sorted,
+ *     no self-loops and no duplicates (checked when BC_VALIDATE is given).  m = nnz / 2.
+ *   - BC values follow the ordered-pair convention of Alg. 1 (every vertex is a source,
+ *     so an undirected pair is counted from both ends): twice the unordered values.
+ *   - Every function returns a bc_status.  Out-parameters are written only on BC_OK.
+ *     bc_last_error() returns this thread's text for the last failure.  No C++
+ *     exception crosses the ABI.
+ *   - Input buffers are caller-owned and only read during the call; the library copies
+ *     what it keeps.  Output buffers are caller-owned.  With BC_DEVICE_PTRS the
+ *     array arguments are device pointers on the context's device (e.g. a torch
+ *     tensor's data_ptr()); otherwise they are host pointers.
+ *   - cuda_stream (nullable; a cudaStream_t) orders the call after prior work on that
+ *     stream; the call returns once its results are complete.
+ *   - Handles are opaque and owned by the library until bc_destroy().
+ */
+#ifndef BC_H_
+#define BC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t bc_status;
+enum {
+  BC_OK = 0,
+  BC_EINVAL = 1,     /* bad argument, malformed CSR, unsupported flag combination */
+  BC_ENOMEM = 2,     /* device or host allocation failed (or exceeds the HBM budget) */
+  BC_EAGAIN = 3,     /* request still running / handle busy */
+  BC_ETIMEDOUT = 4,  /* a bounded device wait gave up, or a poll timed out */
+  BC_ECUDA = 5,      /* CUDA runtime error */
+  BC_ENOTFOUND = 6,  /* unknown request id */
+  BC_ECANCELED = 7   /* request was cancelled */
+};
+
+/* ---- flags ------------------------------------------------------------------------ */
+#define BC_DEVICE_PTRS    (1u << 0)  /* array arguments are device pointers            */
+#define BC_VALIDATE       (1u << 1)  /* bc_graph_create: check the CSR invariants       */
+#define BC_PRUNE_DEG1     (1u << 2)  /* bc_exact: 1-degree reduction (Eq. 3/4, Alg. 6)  */
+#define BC_PATH_PLAIN     (1u << 3)  /* force the per-source path (one BFS per source)  */
+#define BC_PATH_TILED     (1u << 4)  /* force the multi-source tile path                */
+#define BC_LOOP_LAUNCH    (1u << 5)  /* tile path: one kernel launch per level phase    */
+#define BC_LOOP_GRAPH     (1u << 6)  /* tile path: level loop replayed as a CUDA graph  */
+/* bits 8..11: tile width selector for BC_PATH_TILED: 0 = autotuned, else 32 << (k-1) */
+#define BC_TILE_SHIFT     8
+#define BC_TILE_MASK      (0xFu << BC_TILE_SHIFT)
+#define BC_TILE(T)        ((uint32_t)((T) == 32 ? 1 : (T) == 64 ? 2 : (T) == 128 ? 3 : (T) == 256 ? 4 : 0) << BC_TILE_SHIFT)
+
+typedef struct bc_ctx bc_ctx;
+typedef struct bc_graph bc_graph;
+
+/* Per-call statistics (all fields written on BC_OK when the pointer is non-null). */
+typedef struct {
+  double seconds;                 /* device time of the traversal (CUDA events)           */
+  int64_t sources;                /* BFS roots processed (multiset count)                 */
+  int64_t teps_sources;           /* sources counted for TEPS (Sec. 4.1, Eq. 5)           */
+  int64_t edges;                  /* m = undirected edges of the input graph              */
+  double gteps;                   /* teps_sources * m / seconds / 1e9                     */
+  int32_t max_depth;              /* deepest BFS level seen                               */
+  int32_t tile_width;             /* sources per launch: 1 = per-source path              */
+  int64_t sigma_overflow_sources; /* sources whose path count passed 2^64 somewhere       */
+  int64_t levels;                 /* BFS levels executed, summed over launches            */
+  int64_t kernel_launches;        /* library kernels launched by the call                 */
+  int64_t reached_vertices;       /* sum over sources of reached vertices                 */
+  int64_t reached_arcs;           /* sum over sources of adjacency entries of reached v.  */
+} bc_stats;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the library's own
+ * device allocations (0 = no cap).  flags: reserved, pass 0. */
+bc_status bc_ctx_create(int device, size_t hbm_budget_bytes, uint32_t flags, bc_ctx **out);
+
+/* Upload a graph (Sec. 2 graph model) and keep it resident.  nnz < 2^31.  With
+ * BC_VALIDATE the CSR is checked (monotone row_ptr, ids in range, no self-loop,
+ * strictly increasing rows, symmetric) and BC_EINVAL is returned on a violation. */
+bc_status bc_graph_create(bc_ctx *ctx, int32_t n, const int32_t *row_ptr,
+                          const int32_t *col_idx, int64_t nnz, uint32_t flags,
+                          bc_graph **out);
+
+/* Exact BC over every source (Alg. 1 outer loop).  bc_out[n] receives the result.
+ * BC_PRUNE_DEG1 applies the 1-degree reduction (Eq. 3, Eq. 4, Alg. 6; one removal
+ * round, Sec. 3.4.1 footnote 1): the BFS runs on the residual graph from the
+ * non-removed vertices only, with exactly the same result. */
+bc_status bc_exact(bc_graph *g, uint32_t flags, double *bc_out, void *cuda_stream,
+                   bc_stats *stats);
+
+/* Sum over a multiset of sources src[k] (each occurrence counted) of delta_s (Eq. 3
+ * restricted to the given roots).  BC_PRUNE_DEG1 is rejected (BC_EINVAL): Eq. 4 is
+ * stated for the full source set only. */
+bc_status bc_sources(bc_graph *g, const int32_t *src, int32_t k, uint32_t flags,
+                     double *bc_out, void *cuda_stream, bc_stats *stats);
+
+/* Single-source shortest-path counting (Alg. 2 / Alg. 3) on the per-source path:
+ * depth[n] (-1 = unreached), sigma[n] = number of shortest paths modulo 2^64, and
+ * sigma_ovf[n] = 1 where the true count is >= 2^64.  Host buffers unless
+ * BC_DEVICE_PTRS. */
+bc_status bc_sssp(bc_graph *g, int32_t s, uint32_t flags, int32_t *depth, uint64_t *sigma,
+                  uint8_t *sigma_ovf);
+
+/* The same quantities for k <= 256 sources computed together by the tile path:
+ * arrays are [k][n] (source-major).  Parity hook for the batched kernels. */
+bc_status bc_tile_sssp(bc_graph *g, const int32_t *src, int32_t k, uint32_t flags,
+                       int32_t *depth, uint64_t *sigma, uint8_t *sigma_ovf);
+
+/* Device-side 1-degree preprocessing (Alg. 6, Eq. 3's omega): omega[n], removed[n]
+ * (1 = leaf taken out), and the residual CSR: res_row_ptr[n+1], res_col_idx (capacity
+ * nnz), *res_nnz.  Vertex ids are kept; removed vertices get residual degree 0. */
+bc_status bc_prune(bc_graph *g, uint32_t flags, int32_t *omega, uint8_t *removed,
+                   int32_t *res_row_ptr, int32_t *res_col_idx, int64_t *res_nnz);
+
+/* ---- autotuner ----------------------------------------------------------------------- */
+typedef struct {
+  int32_t tile_width;     /* 32, 64, 128 or 256 (0 = per-source path is faster)      */
+  float alpha;            /* top-down -> bottom-up when frontier arcs > alpha * unvisited arcs */
+  float beta;             /* bottom-up -> top-down when frontier vertices < n / beta  */
+  int32_t loop_mode;      /* 0 persistent kernel, 1 per-level launches, 2 CUDA graph  */
+  double probe_seconds;   /* time the tuner spent                                      */
+} bc_tune_result;
+
+/* Time the candidate configurations on a small seeded probe of sources and cache the
+ * winner on the graph (later bc_exact / bc_sources calls without an explicit tile
+ * selector use it).  probe_sources = 0 picks a default. */
+bc_status bc_autotune(bc_graph *g, int32_t probe_sources, uint64_t seed, bc_tune_result *out);
+
+/* ---- serving: continuous batching of BC requests ------------------------------------- */
+enum { BC_REQ_EXACT_LIST = 0, BC_REQ_SAMPLED = 1 };
+
+typedef struct {
+  bc_graph *graph;        /* a graph created on the same context                      */
+  int32_t mode;           /* BC_REQ_EXACT_LIST: src[k]; BC_REQ_SAMPLED: k sources drawn */
+  int32_t k;              /* number of sources                                        */
+  const int32_t *src;     /* host array, copied at submit (EXACT_LIST)                */
+  uint64_t seed;          /* SAMPLED: seed of the draw                                */
+  double *bc_out;         /* host buffer [n], written before the request completes    */
+} bc_request;
+
+typedef struct {
+  bc_status status;       /* BC_OK, or the failure                                    */
+  double queue_seconds;   /* submit -> first tile started                             */
+  double latency_seconds; /* submit -> completion                                     */
+  double scale;           /* SAMPLED: n_nonisolated / k (estimator scale); else 1.0   */
+  int64_t sources;        /* sources processed                                        */
+} bc_result;
+
+/* Enqueue a request; returns at once with *request_id.  The scheduler admits it when
+ * its device footprint fits the context budget, merges its sources with those of
+ * other requests on the same graph into shared tiles and overlaps work on several
+ * streams.  SAMPLED draws k distinct non-isolated sources from `seed` (SplitMix64
+ * stream); bc_out holds the raw sum of delta_s over the drawn sources. */
+bc_status bc_stream_submit(bc_ctx *ctx, const bc_request *req, uint64_t *request_id);
+
+/* Wait up to timeout_us (0 = do not wait, <0 = forever) for a request.  Returns
+ * BC_EAGAIN while it runs; BC_OK once finished (res filled, id released). */
+bc_status bc_stream_poll(bc_ctx *ctx, uint64_t request_id, int32_t timeout_us, bc_result *res);
+
+/* Cancel a queued request (a running one finishes its current tile first). */
+bc_status bc_stream_cancel(bc_ctx *ctx, uint64_t request_id);
+
+/* Destroy a graph or a context.  A graph with requests in flight returns BC_EAGAIN;
+ * destroying a context destroys its graphs and stops its scheduler. */
+bc_status bc_destroy(void *handle);
+
+/* Copy this thread's last error text into buf (always NUL-terminated). */
+void bc_last_error(char *buf, size_t len);
+
+/* Library version string. */
+const char *bc_version(void);
+
+/* Testing hook: device-wait limit in milliseconds for bounded spins (grid barriers);
+ * 0 makes every wait give up at once so the BC_ETIMEDOUT path can be exercised. */
+bc_status bc_set_wait_limit_ms(bc_ctx *ctx, int64_t ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BC_H_ */

@@ -1,0 +1,1652 @@
+// Multi-source tile path: T = 32 * G sources per launch (G = 1, 2, 4, 8).
+//
+// The method is Brandes' (Alg. 1) with the level-synchronous forward sweep of Alg. 2 /
+// Alg. 3 and the successor-checking backward sweep of Alg. 4 / Alg. 5, run for T sources
+// at once.  Per vertex the tile keeps T-bit masks (one 32-bit word per group of 32
+// sources): visited, the frontier of a level (three rotating buffers, reused as the
+// dense level masks of the backward sweep) and sigma overflow; per (vertex, source) it
+// keeps sigma mod 2^64 and r = (1 + delta + omega) / sigma, laid out [n][T] so that the
+// 32 sources of a group are 32 consecutive words read by the 32 lanes of a warp.
+//
+// Forward level l:
+//   * top-down (small frontiers): a marking pass over the edges of the active vertices
+//     A_{l-1} flags every neighbour w with F[p] & ~vis[w] != 0 as a candidate;
+//   * bottom-up (large frontiers): every vertex not yet visited by all sources is a
+//     candidate;
+//   * pull: each candidate w sums, lane by lane, sigma over all neighbours p whose frontier
+//     mask has the lane's bit (all parents at level l-1, no early exit, so sigma is
+//     exact), sets its new mask and is appended to A_l.  No sigma atomics are needed.
+// Backward level d (Alg. 5 with updateDep): each entry (w, M_w) of A_d sums r[v] over the
+// neighbours v whose level-(d+1) mask shares bits with M_w; then delta = sigma * sum,
+// BC[w] += sum over lanes of (omega[s]+1) * delta (fixed lane order) and r[w] = (1 +
+// delta + omega[w]) / sigma.
+//
+// Work mapping (active-edge parallelism, Sec. 3.1): every list that is walked (active
+// vertices, candidates, all vertices) carries an exclusive degree prefix, produced by the
+// packed (count, edges) append counter or built once per graph.  A warp takes an equal
+// slice of the concatenated adjacency, snapped to list-entry starts so each entry belongs
+// to one warp, and maps edge -> entry by a search in the prefix.  Lanes are edges for the
+// frontier-mask tests and sources for the sigma / r row gathers of the edges that hit.
+// Vertices of degree >= kHub are skipped by the walk and processed by a whole CTA
+// (shared-memory reduction in warp order).  All sums run in a fixed order, so the tile
+// path is deterministic.
+//
+// sigma beyond 2^64: a tile first runs with r computed from sigma mod 2^64; if any count
+// overflowed, the tile is rerun (before any BC update) in extended mode, where each
+// overflowed (vertex, source) also carries sigma as a double mantissa and int exponent.
+//
+// Three ways to run the level loop over the same phase bodies: a persistent cooperative
+// kernel with bounded grid barriers (loop_mode 0), one launch per phase (1), and the
+// per-phase launches of kLevelsPerChunk levels captured once as a CUDA graph and
+// replayed until the level loop ends (2).
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "bc_internal.h"
+#include "bc_scan.cuh"
+
+namespace bcl {
+
+namespace {
+
+constexpr int kMaxWarps = 32;       // CTA reduction scratch is sized for 1024 threads
+constexpr int kHub = 2048;          // degree from which a vertex is processed by a whole CTA
+constexpr int kLevelsPerChunk = 8;  // levels per launched chunk / captured graph
+constexpr int BCD_NEEDEXT = 4;      // device code: rerun the tile in extended mode
+
+template <int G>
+struct TPB {  // threads per CTA: wide tiles keep more state per lane
+  static constexpr int value = G >= 4 ? 512 : 1024;
+};
+
+struct TileCtl {
+  GridSync bar;
+  unsigned long long apack[3];  // per-level append counter of A: count << 32 | edges (slot l % 3)
+  unsigned long long cpack[3];  // per-level candidates C: count << 32 | edges (slot l % 3)
+  int chcnt[3];                 // per-level hub candidates (slot l % 3)
+  int ovf_any;                  // some sigma of this tile passed 2^64
+  unsigned ovf_lanes[8];        // lanes (sources) with an overflowed sigma
+  // launched / graph mode registers
+  int level, mode, done, lmax, dlevel;
+  int a_pp, a_lo, a_hi, ecnt;
+  long long levels;
+  unsigned long long ns[256];   // Eq. 3 component size per lane (leaf term)
+};
+
+// shared-memory scratch of the CTA reductions (hubs)
+constexpr size_t kSmemTile = (size_t)kMaxWarps * 32 * (8 + 8 + 4 + 4) + kMaxWarps * 4 + 64;
+
+}  // namespace
+
+struct TileWS {
+  int n = 0, T = 0, G = 0;
+  int64_t capA = 0;
+  bool ext_arrays = false;
+  bool ext_sticky = false;  // this graph needed extended sigma before: start tiles in it
+  uint32_t *vis = nullptr, *F = nullptr, *ovf = nullptr, *cand = nullptr;
+  unsigned long long *sig = nullptr;
+  double *r = nullptr, *xm = nullptr;
+  int32_t *xe = nullptr;
+  int32_t *A = nullptr, *ACD = nullptr;
+  uint32_t *AM = nullptr;
+  int32_t *Aoff = nullptr;
+  int32_t *C = nullptr, *CPD = nullptr, *Ch = nullptr;
+  double *wsrc = nullptr;
+  TileCtl *ctl = nullptr;
+  size_t bytes_main = 0, bytes_ext = 0, bytes_A = 0;
+  // per-graph lists: hubs (degree >= kHub) and the bottom-up walk list (others, deg > 0)
+  const int32_t *lists_for = nullptr;
+  int32_t *hubs = nullptr, *Lbu = nullptr, *PDbu = nullptr;
+  int nhubs = 0, nbu = 0, Ebu = 0;
+  size_t bytes_lists = 0;
+};
+
+namespace {
+
+struct TK {
+  int n;
+  long long nnz;
+  int nsrc;
+  const int32_t *__restrict__ rp;
+  const int32_t *__restrict__ ci;
+  const int32_t *__restrict__ omega;
+  const int32_t *__restrict__ src;
+  double *bc;
+  int leaf_term;
+  uint32_t *vis, *F, *ovf, *cand;
+  unsigned long long *sig;
+  double *r, *xm;
+  int32_t *xe;
+  int32_t *A, *ACD;
+  uint32_t *AM;
+  long long capA;
+  int32_t *Aoff;
+  int32_t *C, *CPD, *Ch;
+  const int32_t *hubs, *Lbu, *PDbu;
+  int nhubs, nbu, Ebu;
+  double *wsrc;
+  TileCtl *ctl;
+  uint32_t unused[8];
+  float alpha;
+  uint64_t limit_ns;
+};
+
+template <int G>
+__device__ __forceinline__ uint32_t *Fbuf(const TK &p, int l) {
+  return p.F + (size_t)(l % 3) * (size_t)p.n * G;
+}
+__device__ __forceinline__ unsigned long long vload64(const unsigned long long *a) {
+  return *(const volatile unsigned long long *)a;
+}
+__device__ __forceinline__ int vdeg(const TK &p, int v) { return p.rp[v + 1] - p.rp[v]; }
+
+// Warp-aggregated append of the flagged lanes' vertices to A with its packed counter.
+__device__ __forceinline__ void append_A(const TK &p, unsigned long long *ctr, int base_off,
+                                         bool flag, int v) {
+  unsigned m = __ballot_sync(BC_FULL, flag);
+  if (!m) return;
+  int deg = flag ? vdeg(p, v) : 0;
+  int tot;
+  int pre = warp_excl_scan(deg, &tot);
+  unsigned long long b = 0;
+  int leader = __ffs(m) - 1;
+  if ((int)lane_id() == leader) b = atomicAdd(ctr, pack_qe(__popc(m), (unsigned)tot));
+  b = __shfl_sync(BC_FULL, b, leader);
+  if (flag) {
+    long long pos = (long long)base_off + (long long)(b >> 32) + __popc(m & lanemask_lt());
+    if (pos < p.capA) {
+      p.A[pos] = v;
+      p.ACD[pos] = (int)(b & 0xffffffffull) + pre;
+    } else {
+      atomicCAS(&p.ctl->bar.err, 0, BCD_CAPACITY);
+    }
+  }
+}
+
+// Per-warp buffer of committed vertices: one atomic per 32 appends.
+struct AppendBuf {
+  int v;  // lane i holds the i-th pending vertex
+  int n;  // pending count (uniform)
+};
+__device__ __forceinline__ void abuf_push(const TK &p, AppendBuf &b, int w,
+                                          unsigned long long *ctr, int base_off) {
+  if ((int)lane_id() == b.n) b.v = w;
+  if (++b.n == 32) {
+    append_A(p, ctr, base_off, true, b.v);
+    b.n = 0;
+  }
+}
+__device__ __forceinline__ void abuf_flush(const TK &p, AppendBuf &b, unsigned long long *ctr,
+                                           int base_off) {
+  append_A(p, ctr, base_off, (int)lane_id() < b.n, b.v);
+  b.n = 0;
+}
+
+// ------------------------------------------------------------------ extended sigma
+struct XS {
+  double m;
+  int e;
+};
+__device__ __forceinline__ XS xs_u64(unsigned long long s) {
+  XS x;
+  x.m = frexp((double)s, &x.e);
+  return x;
+}
+__device__ __forceinline__ void xs_add(XS &a, XS b) {
+  if (b.m == 0.0) return;
+  if (a.m == 0.0) { a = b; return; }
+  if (b.e > a.e) {
+    a.m = ldexp(a.m, a.e - b.e) + b.m;
+    a.e = b.e;
+  } else {
+    a.m += ldexp(b.m, b.e - a.e);
+  }
+}
+__device__ __forceinline__ XS xs_norm(XS a) {
+  int de;
+  a.m = frexp(a.m, &de);
+  a.e += de;
+  return a;
+}
+__device__ __forceinline__ XS sig_xs(const TK &p, size_t idx, bool o) {
+  if (o) {
+    XS x;
+    x.m = p.xm[idx];
+    x.e = p.xe[idx];
+    return x;
+  }
+  return xs_u64(p.sig[idx]);
+}
+
+// ------------------------------------------------------------------ the edge walk
+// Largest i in [lo, hi) with PD[i] <= x (PD non-decreasing, PD[lo] <= x).
+__device__ __forceinline__ int find_owner(const int32_t *PD, int lo, int hi, int x) {
+  const int lane = lane_id();
+  while (hi - lo > 32) {
+    int stride = (hi - lo + 31) / 32;
+    int pos = lo + lane * stride;
+    unsigned b = __ballot_sync(BC_FULL, pos < hi && PD[pos] <= x);
+    lo = lo + (31 - __clz(b)) * stride;
+    hi = min(lo + stride, hi);
+  }
+  int pos = lo + lane;
+  unsigned b = __ballot_sync(BC_FULL, pos < hi && PD[pos] <= x);
+  return lo + (31 - __clz(b));
+}
+
+// Walk the adjacency of list entries [i_lo, i_hi) (entry i: vertex L[i] whose edges
+// start at the level-relative prefix PD[i]; E edges in all).  The warp's slice of edges is
+// snapped to entry starts, so each entry is walked by exactly one warp.  With SKIP_HUBS,
+// entries of degree >= kHub are jumped over.  f(valid, k, w, col) is called once per
+// 32-edge step (lane = edge) with the warp converged: k = entry, w = its vertex, col =
+// position of the edge in col_idx.
+template <bool SKIP_HUBS, typename F>
+__device__ __forceinline__ void walk(const TK &p, const int32_t *L, const int32_t *PD, int i_lo,
+                                     int i_hi, int E, int gwarp, int nwarps, F &&f) {
+  const int lane = lane_id();
+  if (E <= 0 || i_hi <= i_lo) return;
+  const long long per = (((long long)E + nwarps - 1) / nwarps + 31) & ~31ll;
+  const long long ebl = (long long)gwarp * per;
+  if (ebl >= E) return;
+  const int eb = (int)ebl, ee = (int)min(ebl + per, (long long)E);
+  int i0 = find_owner(PD, i_lo, i_hi, eb);
+  if (PD[i0] < eb) i0++;
+  if (i0 >= i_hi || PD[i0] >= ee) return;
+  const int i1 = (ee >= E) ? i_hi : find_owner(PD, i0, i_hi, ee - 1) + 1;
+  const int e_end = (i1 < i_hi) ? PD[i1] : E;
+  int base = i0, e = PD[i0];
+  while (e < e_end) {
+    if (SKIP_HUBS && PD[base] == e && vdeg(p, L[base]) >= kHub) {
+      base++;
+      e = (base < i1) ? PD[base] : e_end;
+      continue;
+    }
+    const int idx = base + lane;
+    const bool in = idx < i1;
+    const int cd = in ? PD[idx] : INT_MAX;
+    const int vv = in ? L[idx] : 0;
+    const int bias = in ? p.rp[vv] - cd : 0;
+    const int cd_after = (base + 32 < i1) ? PD[base + 32] : e_end;
+    const int my = e + lane;
+    const int j = warp_owner(cd, my);
+    const int w = __shfl_sync(BC_FULL, vv, j);
+    const int col = my + __shfl_sync(BC_FULL, bias, j);
+    bool valid = my < e_end;
+    if (SKIP_HUBS && valid) valid = vdeg(p, w) < kHub;
+    f(valid, base + j, w, col);
+    const int j31 = __shfl_sync(BC_FULL, j, 31);
+    int nxt = __shfl_sync(BC_FULL, cd, min(j31 + 1, 31));
+    if (j31 == 31) nxt = cd_after;
+    const int nb = base + j31 + ((e + 32 >= nxt) ? 1 : 0);
+    e += 32;
+    base = nb;
+    if (SKIP_HUBS && e < e_end && base < i1 && vdeg(p, L[base]) >= kHub) {
+      base++;
+      e = (base < i1) ? PD[base] : e_end;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ forward pull
+template <int G, bool EXT>
+struct PullAcc {
+  unsigned long long s[G];
+  uint32_t o;  // per-lane overflow bits, bit g
+  uint32_t newm[G];
+  XS x[EXT ? G : 1];
+};
+
+template <int G, bool EXT>
+__device__ __forceinline__ void pull_init(PullAcc<G, EXT> &a) {
+  a.o = 0u;
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    a.s[g] = 0ull;
+    a.newm[g] = 0u;
+    if (EXT) {
+      a.x[g].m = 0.0;
+      a.x[g].e = 0;
+    }
+  }
+}
+
+// Add the sigma row of frontier vertex pn (lane masks m) to the accumulator.
+template <int G, bool EXT>
+__device__ __forceinline__ void pull_hit(const TK &p, int pn, const uint32_t (&m)[G],
+                                         PullAcc<G, EXT> &a) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    a.newm[g] |= m[g];
+    if ((m[g] >> lane) & 1u) {
+      const size_t idx = (size_t)pn * (32 * G) + 32 * g + lane;
+      const unsigned long long sv = p.sig[idx];
+      const unsigned long long old = a.s[g];
+      a.s[g] = old + sv;
+      const bool po = (p.ovf[(size_t)pn * G + g] >> lane) & 1u;
+      if (a.s[g] < old || po) a.o |= 1u << g;
+      if (EXT) {
+        XS y;
+        if (po) {
+          y.m = p.xm[idx];
+          y.e = p.xe[idx];
+        } else {
+          y = xs_u64(sv);
+        }
+        xs_add(a.x[g], y);
+      }
+    }
+  }
+}
+
+// Store the pulled sigma of w for the lanes that reached it at this level and set its
+// vis / F / ovf words (lane g writes word g).  Returns whether any lane reached w.
+template <int G, bool EXT>
+__device__ __forceinline__ bool pull_commit(const TK &p, int w, int level, const PullAcc<G, EXT> &a,
+                                            const uint32_t (&visw)[G], bool leaf,
+                                            unsigned long long (&nsacc)[G]) {
+  const int lane = lane_id();
+  bool any = false;
+  uint32_t *Fn = Fbuf<G>(p, level);
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    const uint32_t m = a.newm[g];
+    if (!m) continue;
+    any = true;
+    const bool mine = (m >> lane) & 1u;
+    const bool og = (a.o >> g) & 1u;
+    const size_t idx = (size_t)w * (32 * G) + 32 * g + lane;
+    if (mine) {
+      p.sig[idx] = a.s[g];
+      if (EXT && og) {
+        XS x = xs_norm(a.x[g]);
+        p.xm[idx] = x.m;
+        p.xe[idx] = x.e;
+      }
+      if (leaf) nsacc[g] += 1ull + (unsigned long long)p.omega[w];
+    }
+    const unsigned ob = __ballot_sync(BC_FULL, mine && og);
+    if (lane == g) {
+      p.vis[(size_t)w * G + g] = visw[g] | m;
+      Fn[(size_t)w * G + g] = m;
+      if (ob) {
+        p.ovf[(size_t)w * G + g] |= ob;
+        p.ctl->ovf_any = 1;
+        atomicOr(&p.ctl->ovf_lanes[g], ob);
+      }
+    }
+  }
+  return any;
+}
+
+template <int G>
+__device__ __forceinline__ bool load_vis(const TK &p, int w, uint32_t (&visw)[G]) {
+  bool full = true;
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    visw[g] = p.vis[(size_t)w * G + g];
+    full &= visw[g] == 0xffffffffu;
+  }
+  return full;
+}
+
+// Forward pull over the walk of list L: lanes test the edges' frontier masks against their
+// owner's unvisited mask, then the hits are summed owner by owner in edge order.
+template <int G, bool EXT>
+__device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_t *PD, int n_list,
+                          int E, int gwarp, int nwarps, AppendBuf &ab, unsigned long long *ap,
+                          int a_base, bool leaf, unsigned long long (&nsacc)[G]) {
+  const uint32_t *Fp = Fbuf<G>(p, level - 1);
+  int cur = -1;
+  uint32_t visc[G];
+  PullAcc<G, EXT> a;
+  pull_init(a);
+#pragma unroll
+  for (int g = 0; g < G; g++) visc[g] = 0u;
+  walk<false>(p, L, PD, 0, n_list, E, gwarp, nwarps, [&](bool valid, int, int w, int col) {
+    uint32_t vw[G], fm[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      vw[g] = 0xffffffffu;
+      fm[g] = 0u;
+    }
+    bool full = true;
+    if (valid) full = load_vis<G>(p, w, vw);
+    int pj = -1;
+    bool hit = false;
+    if (valid && !full) {
+      pj = p.ci[col];
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        fm[g] = Fp[(size_t)pj * G + g];
+        hit |= (fm[g] & ~vw[g]) != 0u;
+      }
+    }
+    unsigned hits = __ballot_sync(BC_FULL, hit);
+    while (hits) {
+      const int jj = __ffs(hits) - 1;
+      hits &= hits - 1;
+      const int wj = __shfl_sync(BC_FULL, w, jj);
+      if (wj != cur) {
+        if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
+          abuf_push(p, ab, cur, ap, a_base);
+        cur = wj;
+#pragma unroll
+        for (int g = 0; g < G; g++) visc[g] = __shfl_sync(BC_FULL, vw[g], jj);
+        pull_init(a);
+      }
+      const int pn = __shfl_sync(BC_FULL, pj, jj);
+      uint32_t m[G];
+#pragma unroll
+      for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, fm[g], jj) & ~visc[g];
+      pull_hit<G, EXT>(p, pn, m, a);
+    }
+  });
+  if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
+    abuf_push(p, ab, cur, ap, a_base);
+}
+
+// Whole-CTA pull of a hub: warps take contiguous slices of the adjacency; warp 0 folds
+// the partial sums in warp order (deterministic) and commits.  Returns (in warp 0)
+// whether any lane reached w.
+template <int G, bool EXT>
+__device__ bool pull_hub_cta(const TK &p, int w, int level, bool leaf,
+                             unsigned long long (&nsacc)[G], unsigned char *smem) {
+  const int lane = lane_id(), wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t visw[G];
+  if (load_vis<G>(p, w, visw)) return false;  // same for every thread of the CTA
+  PullAcc<G, EXT> a;
+  pull_init(a);
+  const uint32_t *Fp = Fbuf<G>(p, level - 1);
+  const int e0 = p.rp[w], e1 = p.rp[w + 1];
+  const int per = ((e1 - e0 + nw - 1) / nw + 31) & ~31;
+  const int lo = min(e1, e0 + wid * per), hi = min(e1, lo + per);
+  for (int base = lo; base < hi; base += 32) {
+    const int jdx = base + lane;
+    const int pj = jdx < hi ? p.ci[jdx] : -1;
+    uint32_t fm[G];
+    bool hit = false;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      fm[g] = pj >= 0 ? Fp[(size_t)pj * G + g] : 0u;
+      hit |= (fm[g] & ~visw[g]) != 0u;
+    }
+    unsigned hits = __ballot_sync(BC_FULL, hit);
+    while (hits) {
+      const int jj = __ffs(hits) - 1;
+      hits &= hits - 1;
+      uint32_t m[G];
+#pragma unroll
+      for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, fm[g], jj) & ~visw[g];
+      pull_hit<G, EXT>(p, __shfl_sync(BC_FULL, pj, jj), m, a);
+    }
+  }
+  unsigned long long *ss = (unsigned long long *)smem;  // [32 warps][32]
+  double *sxm = (double *)(ss + kMaxWarps * 32);       // [32][32]
+  uint32_t *so = (uint32_t *)(sxm + kMaxWarps * 32);    // [32][32]
+  int *sxe = (int *)(so + kMaxWarps * 32);              // [32][32]
+  uint32_t *sm = (uint32_t *)(sxe + kMaxWarps * 32);    // [32]
+#pragma unroll 1
+  for (int g = 0; g < G; g++) {
+    __syncthreads();
+    ss[wid * 32 + lane] = a.s[g];
+    so[wid * 32 + lane] = (a.o >> g) & 1u;
+    if (lane == 0) sm[wid] = a.newm[g];
+    if (EXT) {
+      sxm[wid * 32 + lane] = a.x[g].m;
+      sxe[wid * 32 + lane] = a.x[g].e;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      unsigned long long s = 0ull;
+      bool o = false;
+      uint32_t m = 0u;
+      XS x;
+      x.m = 0.0;
+      x.e = 0;
+      for (int k = 0; k < nw; k++) {
+        const unsigned long long old = s;
+        s += ss[k * 32 + lane];
+        o |= (s < old) || so[k * 32 + lane] != 0u;
+        m |= sm[k];
+        if (EXT) {
+          XS y;
+          y.m = sxm[k * 32 + lane];
+          y.e = sxe[k * 32 + lane];
+          xs_add(x, y);
+        }
+      }
+      a.s[g] = s;
+      a.o = (a.o & ~(1u << g)) | ((o ? 1u : 0u) << g);
+      a.newm[g] = m;
+      if (EXT) a.x[g] = x;
+    }
+  }
+  bool any = false;
+  if (wid == 0) any = pull_commit<G, EXT>(p, w, level, a, visw, leaf, nsacc);
+  __syncthreads();
+  return any;
+}
+
+// ------------------------------------------------------------------ forward phases
+template <int G>
+__device__ void phase_init_vis(const TK &p, int gtid, int nthr) {
+  for (long long i = gtid; i < (long long)p.n * G; i += nthr) p.vis[i] = p.unused[i % G];
+}
+
+// The tile's sources become A_0 (distinct vertices with at least one edge; a repeated
+// source sets several lanes of one vertex).  Single thread.
+template <int G>
+__device__ void init_sources(const TK &p) {
+  unsigned cnt = 0, edges = 0;
+  uint32_t *F0 = Fbuf<G>(p, 0);
+  for (int t = 0; t < p.nsrc; t++) {
+    const int s = p.src[t];
+    const int g = t >> 5;
+    const uint32_t bit = 1u << (t & 31);
+    const int ds = vdeg(p, s);
+    bool first = true;
+    for (int h = 0; h < G; h++) first &= (p.vis[(size_t)s * G + h] & ~p.unused[h]) == 0u;
+    p.vis[(size_t)s * G + g] |= bit;
+    p.sig[(size_t)s * (32 * G) + t] = 1ull;
+    if (ds > 0) {
+      F0[(size_t)s * G + g] |= bit;
+      if (first) {
+        p.A[cnt] = s;
+        p.ACD[cnt] = (int)edges;
+        cnt++;
+        edges += (unsigned)ds;
+      }
+    }
+    if (p.leaf_term && p.omega) p.ctl->ns[t] = 1ull + (unsigned long long)p.omega[s];
+  }
+  p.ctl->apack[0] = pack_qe(cnt, edges);
+  p.ctl->apack[1] = p.ctl->apack[2] = 0ull;
+  p.ctl->cpack[0] = p.ctl->cpack[1] = p.ctl->cpack[2] = 0ull;
+  p.ctl->chcnt[0] = p.ctl->chcnt[1] = p.ctl->chcnt[2] = 0;
+  p.Aoff[0] = 0;
+  p.Aoff[1] = (int)cnt;
+}
+
+// Masks of A_{l-1} into AM; clear F of A_{l-2}.
+template <int G>
+__device__ void phase_keep(const TK &p, int level, int a_pp, int a0, int a1, int gtid, int nthr) {
+  const uint32_t *Fp = Fbuf<G>(p, level - 1);
+  for (long long i = (long long)a0 * G + gtid; i < (long long)a1 * G; i += nthr)
+    p.AM[i] = Fp[(size_t)p.A[i / G] * G + (i % G)];
+  if (level >= 2) {
+    uint32_t *Fc = Fbuf<G>(p, level - 2);
+    for (long long i = (long long)a_pp * G + gtid; i < (long long)a0 * G; i += nthr)
+      Fc[(size_t)p.A[i / G] * G + (i % G)] = 0u;
+  }
+}
+
+// Top-down marking of the candidates of level l: edges of A_{l-1} (unsnapped equal
+// slices; an edge's owner is found in the prefix ACD).  Each new candidate is appended to
+// C with its degree prefix, or to Ch if it is a hub.
+template <int G>
+__device__ void phase_mark(const TK &p, int level, int a0, int a1, int E1, int gwarp, int nwarps) {
+  const int lane = lane_id();
+  if (E1 <= 0) return;
+  const long long per = (((long long)E1 + nwarps - 1) / nwarps + 31) & ~31ll;
+  const long long eb = (long long)gwarp * per;
+  if (eb >= E1) return;
+  const int ee = (int)min(eb + per, (long long)E1);
+  const uint32_t *Fp = Fbuf<G>(p, level - 1);
+  int base = find_owner(p.ACD, a0, a1, (int)eb);
+  unsigned long long *cp = &p.ctl->cpack[level % 3];
+  int *chp = &p.ctl->chcnt[level % 3];
+  for (int e = (int)eb; e < ee; e += 32) {
+    const int idx = base + lane;
+    const bool in = idx < a1;
+    const int cdj = in ? p.ACD[idx] : INT_MAX;
+    const int vj = in ? p.A[idx] : 0;
+    const int bias = in ? p.rp[vj] - cdj : 0;
+    const int cd_after = (base + 32 < a1) ? p.ACD[base + 32] : E1;
+    const int my = e + lane;
+    const int j = warp_owner(cdj, my);
+    const int v = __shfl_sync(BC_FULL, vj, j);
+    const int col = my + __shfl_sync(BC_FULL, bias, j);
+    bool isc = false;
+    int w = 0;
+    if (my < ee) {
+      w = p.ci[col];
+      bool hit = false;
+#pragma unroll
+      for (int g = 0; g < G; g++) hit |= (Fp[(size_t)v * G + g] & ~p.vis[(size_t)w * G + g]) != 0u;
+      if (hit) {
+        const uint32_t bit = 1u << (w & 31);
+        isc = !(atomicOr(p.cand + (w >> 5), bit) & bit);
+      }
+    }
+    const int dw = isc ? vdeg(p, w) : 0;
+    const bool hub = isc && dw >= kHub;
+    const bool nrm = isc && !hub;
+    const unsigned mn = __ballot_sync(BC_FULL, nrm), mh = __ballot_sync(BC_FULL, hub);
+    if (mn) {
+      int tot;
+      const int pre = warp_excl_scan(nrm ? dw : 0, &tot);
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(cp, pack_qe(__popc(mn), (unsigned)tot));
+      b = __shfl_sync(BC_FULL, b, 0);
+      if (nrm) {
+        const int pos = (int)(b >> 32) + __popc(mn & lanemask_lt());
+        p.C[pos] = w;
+        p.CPD[pos] = (int)(b & 0xffffffffull) + pre;
+      }
+    }
+    if (mh) {
+      int b = 0;
+      if (lane == 0) b = atomicAdd(chp, __popc(mh));
+      b = __shfl_sync(BC_FULL, b, 0);
+      if (hub) p.Ch[b + __popc(mh & lanemask_lt())] = w;
+    }
+    const int j31 = __shfl_sync(BC_FULL, j, 31);
+    int nxt = __shfl_sync(BC_FULL, cdj, min(j31 + 1, 31));
+    if (j31 == 31) nxt = cd_after;
+    base += j31 + ((e + 32 >= nxt) ? 1 : 0);
+  }
+}
+
+// Pull of level l: hubs (Ch, or every hub in bottom-up mode) by whole CTAs, then the walk
+// over C (top-down) or over every non-hub vertex (bottom-up).  Reached vertices go to A_l.
+template <int G, bool EXT>
+__device__ void phase_pull(const TK &p, int level, bool bu, int a_base, int gwarp, int nwarps,
+                           unsigned char *smem) {
+  const int lane = lane_id();
+  const bool leaf = p.leaf_term && p.omega;
+  unsigned long long nsacc[G];
+#pragma unroll
+  for (int g = 0; g < G; g++) nsacc[g] = 0ull;
+  unsigned long long *ap = &p.ctl->apack[level % 3];
+  const int nh = bu ? p.nhubs : *(volatile int *)&p.ctl->chcnt[level % 3];
+  const int32_t *hl = bu ? p.hubs : p.Ch;
+  for (int i = blockIdx.x; i < nh; i += gridDim.x) {
+    const int w = hl[i];
+    const bool any = pull_hub_cta<G, EXT>(p, w, level, leaf, nsacc, smem);
+    if ((threadIdx.x >> 5) == 0) append_A(p, ap, a_base, any && lane == 0, w);
+  }
+  AppendBuf ab;
+  ab.v = 0;
+  ab.n = 0;
+  if (bu) {
+    pull_walk<G, EXT>(p, level, p.Lbu, p.PDbu, p.nbu, p.Ebu, gwarp, nwarps, ab, ap, a_base, leaf, nsacc);
+  } else {
+    const unsigned long long cpk = vload64(&p.ctl->cpack[level % 3]);
+    const int nc = (int)(cpk >> 32);
+    pull_walk<G, EXT>(p, level, p.C, p.CPD, nc, (int)(cpk & 0xffffffffull), gwarp, nwarps, ab, ap,
+                      a_base, leaf, nsacc);
+    // clear the candidate bits of this level (C and Ch)
+    for (int i = gwarp * 32 + lane; i < nc; i += nwarps * 32) {
+      const int w = p.C[i];
+      atomicAnd(p.cand + (w >> 5), ~(1u << (w & 31)));
+    }
+    for (int i = gwarp * 32 + lane; i < nh; i += nwarps * 32) {
+      const int w = p.Ch[i];
+      atomicAnd(p.cand + (w >> 5), ~(1u << (w & 31)));
+    }
+  }
+  abuf_flush(p, ab, ap, a_base);
+  if (leaf) {
+#pragma unroll
+    for (int g = 0; g < G; g++)
+      if (nsacc[g]) atomicAdd(&p.ctl->ns[32 * g + lane], nsacc[g]);
+  }
+}
+
+// ------------------------------------------------------------------ backward phases
+// r of the deepest level's (vertex, source) pairs: delta = 0 there.
+template <int G, bool EXT>
+__device__ void phase_bwd_deep(const TK &p, int a0, int a1, int gtid, int nthr) {
+  for (long long i = (long long)a0 * 32 * G + gtid; i < (long long)a1 * 32 * G; i += nthr) {
+    const int k = (int)(i / (32 * G)), t = (int)(i % (32 * G)), g = t >> 5, ln = t & 31;
+    const uint32_t m = p.AM[(size_t)k * G + g];
+    if (!((m >> ln) & 1u)) continue;
+    const int w = p.A[k];
+    const double om = p.omega ? (double)p.omega[w] : 0.0;
+    const size_t idx = (size_t)w * (32 * G) + t;
+    double sg;
+    if (EXT) {
+      const bool o = (p.ovf[(size_t)w * G + g] >> ln) & 1u;
+      const XS x = sig_xs(p, idx, o);
+      sg = x.m;
+      if (!o) p.xe[idx] = x.e;
+    } else {
+      sg = (double)p.sig[idx];
+    }
+    p.r[idx] = (1.0 + om) / sg;
+  }
+}
+
+template <int G, bool EXT>
+struct BwdOwner {
+  uint32_t mw[G];
+  double sg[G];
+  int ew[EXT ? G : 1];
+  double acc[G];
+};
+
+template <int G, bool EXT>
+__device__ __forceinline__ void bwd_start(const TK &p, int k, BwdOwner<G, EXT> &o) {
+  const int lane = lane_id();
+  const int w = p.A[k];
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    o.mw[g] = p.AM[(size_t)k * G + g];
+    o.sg[g] = 1.0;
+    o.acc[g] = 0.0;
+    if (EXT) o.ew[g] = 0;
+    if ((o.mw[g] >> lane) & 1u) {
+      const size_t idx = (size_t)w * (32 * G) + 32 * g + lane;
+      if (EXT) {
+        const bool ov = (p.ovf[(size_t)w * G + g] >> lane) & 1u;
+        const XS x = sig_xs(p, idx, ov);
+        o.sg[g] = x.m;
+        o.ew[g] = x.e;
+      } else {
+        o.sg[g] = (double)p.sig[idx];
+      }
+    }
+  }
+}
+
+template <int G, bool EXT>
+__device__ __forceinline__ void bwd_hit(const TK &p, int v, const uint32_t (&m)[G], BwdOwner<G, EXT> &o) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    if ((m[g] >> lane) & 1u) {
+      const size_t idx = (size_t)v * (32 * G) + 32 * g + lane;
+      double x = p.r[idx];
+      if (EXT) x = ldexp(x, o.ew[g] - p.xe[idx]);
+      o.acc[g] += x;
+    }
+  }
+}
+
+template <int G, bool EXT>
+__device__ __forceinline__ void bwd_commit(const TK &p, int w, const BwdOwner<G, EXT> &o) {
+  const int lane = lane_id();
+  const double om = p.omega ? (double)p.omega[w] : 0.0;
+  double contrib = 0.0;
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    if ((o.mw[g] >> lane) & 1u) {
+      const size_t idx = (size_t)w * (32 * G) + 32 * g + lane;
+      const double delta = o.sg[g] * o.acc[g];
+      contrib += p.wsrc[32 * g + lane] * delta;
+      p.r[idx] = (1.0 + delta + om) / o.sg[g];
+      if (EXT) p.xe[idx] = o.ew[g];
+    }
+  }
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) contrib += __shfl_xor_sync(BC_FULL, contrib, s);
+  if (lane == 0 && contrib != 0.0) p.bc[w] += contrib;
+}
+
+// Backward walk over A_d (hubs skipped): every entry is committed once, in entry order,
+// with the r rows of its successors summed in edge order.
+template <int G, bool EXT>
+__device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn, int gwarp, int nwarps) {
+  int cur = -1;
+  BwdOwner<G, EXT> o;
+  walk<true>(p, p.A, p.ACD, a0, a1, E, gwarp, nwarps, [&](bool valid, int k, int, int col) {
+    uint32_t dm[G];
+    bool hit = false;
+    int v = -1;
+#pragma unroll
+    for (int g = 0; g < G; g++) dm[g] = 0u;
+    if (valid) {
+      v = p.ci[col];
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        dm[g] = Dn[(size_t)v * G + g];
+        hit |= (dm[g] & p.AM[(size_t)k * G + g]) != 0u;
+      }
+    }
+    const unsigned vm = __ballot_sync(BC_FULL, valid);
+    const unsigned hits = __ballot_sync(BC_FULL, hit);
+    if (!vm) return;
+    const int k_lo = __shfl_sync(BC_FULL, k, __ffs(vm) - 1);
+    const int k_hi = __shfl_sync(BC_FULL, k, 31 - __clz(vm));
+    for (int kk = k_lo; kk <= k_hi; kk++) {
+      const unsigned lanes_k = __ballot_sync(BC_FULL, valid && k == kk);
+      if (!lanes_k) continue;  // a hub entry inside the step
+      if (kk != cur) {
+        if (cur >= 0) bwd_commit<G, EXT>(p, p.A[cur], o);
+        cur = kk;
+        bwd_start<G, EXT>(p, kk, o);
+      }
+      unsigned h = hits & lanes_k;
+      while (h) {
+        const int jj = __ffs(h) - 1;
+        h &= h - 1;
+        uint32_t m[G];
+#pragma unroll
+        for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, dm[g], jj) & o.mw[g];
+        bwd_hit<G, EXT>(p, __shfl_sync(BC_FULL, v, jj), m, o);
+      }
+    }
+  });
+  if (cur >= 0) bwd_commit<G, EXT>(p, p.A[cur], o);
+}
+
+template <int G, bool EXT>
+__device__ void bwd_hub_cta(const TK &p, int k, const uint32_t *Dn, unsigned char *smem) {
+  const int lane = lane_id(), wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int w = p.A[k];
+  BwdOwner<G, EXT> o;
+  bwd_start<G, EXT>(p, k, o);
+  const int e0 = p.rp[w], e1 = p.rp[w + 1];
+  const int per = ((e1 - e0 + nw - 1) / nw + 31) & ~31;
+  const int lo = min(e1, e0 + wid * per), hi = min(e1, lo + per);
+  for (int base = lo; base < hi; base += 32) {
+    const int jdx = base + lane;
+    const int v = jdx < hi ? p.ci[jdx] : -1;
+    uint32_t dm[G];
+    bool hit = false;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      dm[g] = v >= 0 ? Dn[(size_t)v * G + g] : 0u;
+      hit |= (dm[g] & o.mw[g]) != 0u;
+    }
+    unsigned hits = __ballot_sync(BC_FULL, hit);
+    while (hits) {
+      const int jj = __ffs(hits) - 1;
+      hits &= hits - 1;
+      uint32_t m[G];
+#pragma unroll
+      for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, dm[g], jj) & o.mw[g];
+      bwd_hit<G, EXT>(p, __shfl_sync(BC_FULL, v, jj), m, o);
+    }
+  }
+  double *sa = (double *)smem;
+#pragma unroll 1
+  for (int g = 0; g < G; g++) {
+    __syncthreads();
+    sa[wid * 32 + lane] = o.acc[g];
+    __syncthreads();
+    if (wid == 0) {
+      double s = 0.0;
+      for (int q = 0; q < nw; q++) s += sa[q * 32 + lane];
+      o.acc[g] = s;
+    }
+  }
+  if (wid == 0) bwd_commit<G, EXT>(p, w, o);
+  __syncthreads();
+}
+
+// Backward level d: hubs of A_d by whole CTAs, the rest by the walk; scatter A_d's masks
+// into the level-d buffer (read at level d-1) and clear A_{d+2}'s masks.  Three distinct
+// buffers, so one barrier per level suffices.
+template <int G, bool EXT>
+__device__ void phase_bwd_level(const TK &p, int d, int a0, int a1, int Ed, int c0, int c1, int gtid,
+                                int nthr, int gwarp, int nwarps, unsigned char *smem) {
+  const uint32_t *Dn = Fbuf<G>(p, d + 1);
+  uint32_t *Dd = Fbuf<G>(p, d);
+  uint32_t *Dc = Fbuf<G>(p, d + 2);
+  for (long long i = (long long)a0 * G + gtid; i < (long long)a1 * G; i += nthr)
+    Dd[(size_t)p.A[i / G] * G + (i % G)] = p.AM[i];
+  for (long long i = (long long)c0 * G + gtid; i < (long long)c1 * G; i += nthr)
+    Dc[(size_t)p.A[i / G] * G + (i % G)] = 0u;
+  for (int k = a0 + blockIdx.x; k < a1; k += gridDim.x)
+    if (vdeg(p, p.A[k]) >= kHub) bwd_hub_cta<G, EXT>(p, k, Dn, smem);
+  bwd_walk<G, EXT>(p, a0, a1, Ed, Dn, gwarp, nwarps);
+}
+
+__device__ void leaf_terms(const TK &p) {
+  if (!(p.leaf_term && p.omega)) return;
+  for (int t = 0; t < p.nsrc; t++) {
+    const int s = p.src[t];
+    const double om = (double)p.omega[s];
+    if (om > 0.0) p.bc[s] += om * (2.0 * (double)p.ctl->ns[t] - om - 3.0);
+  }
+}
+
+// edges of A_d: the level-relative prefix of its last entry plus that entry's degree
+__device__ __forceinline__ int level_edges(const TK &p, int a0, int a1) {
+  if (a1 <= a0) return 0;
+  return p.ACD[a1 - 1] + vdeg(p, p.A[a1 - 1]);
+}
+
+// ------------------------------------------------------------------ persistent kernel
+template <int G, bool EXT>
+__global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fwd_only) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nthr = gridDim.x * blockDim.x;
+  const int gwarp = gtid >> 5, nwarps = nthr >> 5;
+  GridSync *gs = &p.ctl->bar;
+  phase_init_vis<G>(p, gtid, nthr);
+  if (!grid_sync(gs, p.limit_ns)) return;
+  if (gtid == 0) init_sources<G>(p);
+  if (!grid_sync(gs, p.limit_ns)) return;
+  int level = 1, a_pp = 0, a_lo = 0, a_hi, ecnt;
+  {
+    const unsigned long long pk = vload64(&p.ctl->apack[0]);
+    a_hi = (int)(pk >> 32);
+    ecnt = (int)(pk & 0xffffffffull);
+  }
+  while (a_hi > a_lo) {
+    const bool bu = (double)ecnt > (double)p.alpha * (double)p.nnz;
+    phase_keep<G>(p, level, a_pp, a_lo, a_hi, gtid, nthr);
+    if (!bu) {
+      phase_mark<G>(p, level, a_lo, a_hi, ecnt, gwarp, nwarps);
+      if (!grid_sync(gs, p.limit_ns)) return;
+    }
+    phase_pull<G, EXT>(p, level, bu, a_hi, gwarp, nwarps, smem);
+    if (gtid == 0) {
+      p.ctl->apack[(level + 1) % 3] = 0ull;
+      p.ctl->cpack[(level + 1) % 3] = 0ull;
+      p.ctl->chcnt[(level + 1) % 3] = 0;
+    }
+    if (!grid_sync(gs, p.limit_ns)) return;
+    const unsigned long long pk = vload64(&p.ctl->apack[level % 3]);
+    a_pp = a_lo;
+    a_lo = a_hi;
+    a_hi = a_lo + (int)(pk >> 32);
+    ecnt = (int)(pk & 0xffffffffull);
+    level++;
+    if (gtid == 0) p.Aoff[level] = a_hi;
+  }
+  const int lmax = level - 2;
+  if (gtid == 0) {
+    p.ctl->lmax = lmax;
+    p.ctl->levels += level - 1;
+  }
+  if (fwd_only) return;
+  if (!EXT && *(volatile int *)&p.ctl->ovf_any) {
+    if (gtid == 0) atomicCAS(&p.ctl->bar.err, 0, BCD_NEEDEXT);
+    return;
+  }
+  if (!grid_sync(gs, p.limit_ns)) return;
+  if (lmax >= 1) {
+    phase_bwd_deep<G, EXT>(p, p.Aoff[lmax], p.Aoff[lmax + 1], gtid, nthr);
+    if (!grid_sync(gs, p.limit_ns)) return;
+    for (int d = lmax - 1; d >= 1; --d) {
+      int c0 = 0, c1 = 0;
+      if (d + 2 <= lmax) {
+        c0 = p.Aoff[d + 2];
+        c1 = p.Aoff[d + 3];
+      }
+      const int a0 = p.Aoff[d], a1 = p.Aoff[d + 1];
+      phase_bwd_level<G, EXT>(p, d, a0, a1, level_edges(p, a0, a1), c0, c1, gtid, nthr, gwarp,
+                              nwarps, smem);
+      if (!grid_sync(gs, p.limit_ns)) return;
+    }
+  }
+  if (gtid == 0) leaf_terms(p);
+}
+
+// ------------------------------------------------------------------ launched kernels
+template <int G>
+__global__ void __launch_bounds__(TPB<G>::value) k_init_vis(TK p) {
+  phase_init_vis<G>(p, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+template <int G>
+__global__ void k_init_src(TK p) {
+  init_sources<G>(p);
+  TileCtl *c = p.ctl;
+  const unsigned long long pk = c->apack[0];
+  c->level = 1;
+  c->a_pp = 0;
+  c->a_lo = 0;
+  c->a_hi = (int)(pk >> 32);
+  c->ecnt = (int)(pk & 0xffffffffull);
+  c->mode = (double)c->ecnt > (double)p.alpha * (double)p.nnz;
+  c->done = c->a_hi == 0;
+  if (c->done) {
+    c->lmax = 0;
+    c->dlevel = 0;
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(TPB<G>::value) k_fwd_mark(TK p) {
+  const TileCtl *c = p.ctl;
+  if (c->done || c->bar.err) return;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  phase_keep<G>(p, c->level, c->a_pp, c->a_lo, c->a_hi, gtid, nthr);
+  if (!c->mode) phase_mark<G>(p, c->level, c->a_lo, c->a_hi, c->ecnt, gtid >> 5, nthr >> 5);
+}
+
+template <int G, bool EXT>
+__global__ void __launch_bounds__(TPB<G>::value, 1) k_fwd_pull(TK p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TileCtl *c = p.ctl;
+  if (c->done || c->bar.err) return;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  phase_pull<G, EXT>(p, c->level, c->mode != 0, c->a_hi, gtid >> 5, nthr >> 5, smem);
+}
+
+__global__ void k_fwd_end(TK p) {
+  TileCtl *c = p.ctl;
+  if (c->done || c->bar.err) return;
+  int level = c->level;
+  const unsigned long long pk = c->apack[level % 3];
+  c->apack[(level + 1) % 3] = 0ull;
+  c->cpack[(level + 1) % 3] = 0ull;
+  c->chcnt[(level + 1) % 3] = 0;
+  c->a_pp = c->a_lo;
+  c->a_lo = c->a_hi;
+  c->a_hi = c->a_lo + (int)(pk >> 32);
+  c->ecnt = (int)(pk & 0xffffffffull);
+  level++;
+  c->level = level;
+  p.Aoff[level] = c->a_hi;
+  c->mode = (double)c->ecnt > (double)p.alpha * (double)p.nnz;
+  if ((long long)c->a_hi > p.capA) {  // appends past the active-list capacity were dropped
+    atomicCAS(&c->bar.err, 0, BCD_CAPACITY);
+    c->done = 1;
+    return;
+  }
+  if (c->a_hi == c->a_lo) {
+    c->done = 1;
+    c->lmax = level - 2;
+    c->levels += level - 1;
+    c->dlevel = level - 3;  // first backward level (lmax - 1)
+  }
+}
+
+template <int G, bool EXT>
+__global__ void __launch_bounds__(TPB<G>::value) k_bwd_deep(TK p) {
+  const TileCtl *c = p.ctl;
+  if (c->lmax < 1 || c->bar.err) return;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  phase_bwd_deep<G, EXT>(p, p.Aoff[c->lmax], p.Aoff[c->lmax + 1], gtid, nthr);
+}
+
+template <int G, bool EXT>
+__global__ void __launch_bounds__(TPB<G>::value, 1) k_bwd_level(TK p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TileCtl *c = p.ctl;
+  const int d = c->dlevel, lmax = c->lmax;
+  if (d < 1 || c->bar.err) return;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  int c0 = 0, c1 = 0;
+  if (d + 2 <= lmax) {
+    c0 = p.Aoff[d + 2];
+    c1 = p.Aoff[d + 3];
+  }
+  const int a0 = p.Aoff[d], a1 = p.Aoff[d + 1];
+  phase_bwd_level<G, EXT>(p, d, a0, a1, level_edges(p, a0, a1), c0, c1, gtid, nthr, gtid >> 5,
+                          nthr >> 5, smem);
+}
+
+__global__ void k_bwd_step(TK p) {
+  if (p.ctl->dlevel >= 1) p.ctl->dlevel--;
+}
+
+__global__ void k_leaf(TK p) {
+  if (!p.ctl->bar.err) leaf_terms(p);
+}
+
+// Export depth / sigma / overflow of the tile's sources, source-major [k][n].
+template <int G>
+__global__ void k_export(TK p, int lmax, int32_t *depth, unsigned long long *sigma, uint8_t *ovf) {
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  for (int t = gtid; t < p.nsrc; t += nthr) {  // the sources themselves (also degree 0)
+    const size_t o = (size_t)t * p.n + p.src[t];
+    depth[o] = 0;
+    sigma[o] = 1ull;
+    ovf[o] = 0;
+  }
+  for (int l = 1; l <= lmax; l++) {
+    const int a0 = p.Aoff[l], a1 = p.Aoff[l + 1];
+    for (long long i = (long long)a0 * 32 * G + gtid; i < (long long)a1 * 32 * G; i += nthr) {
+      const int k = (int)(i / (32 * G)), t = (int)(i % (32 * G));
+      if (t >= p.nsrc) continue;
+      const int w = p.A[k];
+      const uint32_t m = p.AM[(size_t)k * G + (t >> 5)];
+      if ((m >> (t & 31)) & 1u) {
+        const size_t o = (size_t)t * p.n + w;
+        depth[o] = l;
+        sigma[o] = p.sig[(size_t)w * (32 * G) + t];
+        ovf[o] = (p.ovf[(size_t)w * G + (t >> 5)] >> (t & 31)) & 1u;
+      }
+    }
+  }
+}
+
+// Per-graph lists: hubs, and the bottom-up walk list (non-hub vertices with an edge).
+__global__ void k_lists(int32_t n, const int32_t *rp, int32_t *hubs, int *nh, int32_t *flag) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int d = rp[v + 1] - rp[v];
+    if (d >= kHub) hubs[atomicAdd(nh, 1)] = v;
+    flag[v] = (d > 0 && d < kHub) ? 1 : 0;
+  }
+}
+__global__ void k_lists_fill(int32_t n, const int32_t *rp, const int32_t *flag, const int32_t *pos,
+                             int32_t *L, int32_t *degs) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    if (flag[v]) {
+      L[pos[v]] = v;
+      degs[pos[v]] = rp[v + 1] - rp[v];
+    }
+}
+
+__global__ void k_wsrc(const int32_t *src, int nsrc, const int32_t *omega, double *wsrc, int T) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < T) wsrc[t] = t < nsrc ? (omega ? (double)omega[src[t]] + 1.0 : 1.0) : 0.0;
+}
+
+// ------------------------------------------------------------------ host dispatch helpers
+struct KPtrs {
+  void *persistent, *pull, *mark, *init_vis, *init_src, *bdeep, *blevel, *exportk;
+  int tpb;
+};
+
+template <int G, bool EXT>
+KPtrs kptrs_t() {
+  return KPtrs{(void *)tile_persistent<G, EXT>, (void *)k_fwd_pull<G, EXT>, (void *)k_fwd_mark<G>,
+               (void *)k_init_vis<G>, (void *)k_init_src<G>, (void *)k_bwd_deep<G, EXT>,
+               (void *)k_bwd_level<G, EXT>, (void *)k_export<G>, TPB<G>::value};
+}
+
+KPtrs kptrs(int G, bool ext) {
+  switch (G) {
+    case 1: return ext ? kptrs_t<1, true>() : kptrs_t<1, false>();
+    case 2: return ext ? kptrs_t<2, true>() : kptrs_t<2, false>();
+    case 4: return ext ? kptrs_t<4, true>() : kptrs_t<4, false>();
+    default: return ext ? kptrs_t<8, true>() : kptrs_t<8, false>();
+  }
+}
+
+bool g_attr_done[2][9];
+
+bc_status set_attrs(int G, bool ext) {
+  if (g_attr_done[ext][G]) return BC_OK;
+  const KPtrs k = kptrs(G, ext);
+  for (void *f : {k.persistent, k.pull, k.blevel})
+    BC_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTile));
+  g_attr_done[ext][G] = true;
+  return BC_OK;
+}
+
+}  // namespace
+
+// ================================================================== host side
+static void ws_release(Ctx *ctx, TileWS *ws, bool main, bool ext, bool A) {
+  if (main && ws->ctl) {
+    void *ptrs[] = {ws->vis, ws->F, ws->ovf, ws->cand, ws->sig, ws->r, ws->Aoff,
+                    ws->C, ws->CPD, ws->Ch, ws->wsrc, ws->ctl};
+    for (void *q : ptrs) cudaFree(q);
+    ctx->mem.release(nullptr, ws->bytes_main);
+    ws->vis = ws->F = ws->ovf = ws->cand = nullptr;
+    ws->sig = nullptr;
+    ws->r = nullptr;
+    ws->Aoff = ws->C = ws->CPD = ws->Ch = nullptr;
+    ws->wsrc = nullptr;
+    ws->ctl = nullptr;
+    ws->bytes_main = 0;
+  }
+  if (ext && ws->ext_arrays) {
+    cudaFree(ws->xm);
+    cudaFree(ws->xe);
+    ctx->mem.release(nullptr, ws->bytes_ext);
+    ws->xm = nullptr;
+    ws->xe = nullptr;
+    ws->ext_arrays = false;
+    ws->bytes_ext = 0;
+  }
+  if (A && ws->A) {
+    cudaFree(ws->A);
+    cudaFree(ws->ACD);
+    cudaFree(ws->AM);
+    ctx->mem.release(nullptr, ws->bytes_A);
+    ws->A = ws->ACD = nullptr;
+    ws->AM = nullptr;
+    ws->bytes_A = 0;
+    ws->capA = 0;
+  }
+}
+
+static void lists_release(Ctx *ctx, TileWS *ws) {
+  if (!ws->hubs) return;
+  cudaFree(ws->hubs);
+  cudaFree(ws->Lbu);
+  cudaFree(ws->PDbu);
+  ctx->mem.release(nullptr, ws->bytes_lists);
+  ws->hubs = ws->Lbu = ws->PDbu = nullptr;
+  ws->lists_for = nullptr;
+  ws->bytes_lists = 0;
+}
+
+void tile_free(Ctx *ctx, TileWS *ws) {
+  if (!ws) return;
+  ws_release(ctx, ws, true, true, true);
+  lists_release(ctx, ws);
+  delete ws;
+}
+
+#define TA(ptr, bytes)                                                             \
+  do {                                                                             \
+    if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes) ? (bytes) : 16); \
+  } while (0)
+
+static bc_status ws_main(Ctx *ctx, TileWS *ws, int n, int T) {
+  if (ws->ctl && ws->n == n && ws->T == T) return BC_OK;
+  ws_release(ctx, ws, true, true, true);
+  const int G = T / 32;
+  const size_t N = (size_t)n, NG = N * G, NT = N * T;
+  const size_t bytes = NG * 4 * 5 + NT * 16 + (N / 32 + 1) * 4 + (N + 3) * 4 + N * 12 + T * 8 +
+                       sizeof(TileCtl);
+  bc_status s = ctx->mem.alloc(nullptr, bytes);
+  if (s) return s;
+  cudaError_t e = cudaSuccess;
+  TA(ws->vis, NG * 4);
+  TA(ws->F, NG * 4 * 3);
+  TA(ws->ovf, NG * 4);
+  TA(ws->cand, (N / 32 + 1) * 4);
+  TA(ws->sig, NT * 8);
+  TA(ws->r, NT * 8);
+  TA(ws->Aoff, (N + 3) * 4);
+  TA(ws->C, N * 4);
+  TA(ws->CPD, N * 4);
+  TA(ws->Ch, N * 4);
+  TA(ws->wsrc, (size_t)T * 8);
+  TA(ws->ctl, sizeof(TileCtl));
+  ws->n = n;
+  ws->T = T;
+  ws->G = G;
+  ws->bytes_main = bytes;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ws_release(ctx, ws, true, false, false);
+    return fail(BC_ENOMEM, std::string("tile workspace allocation failed: ") + cudaGetErrorString(e));
+  }
+  BC_CUDA_TRY(cudaMemset(ws->cand, 0, (N / 32 + 1) * 4));
+  return BC_OK;
+}
+
+static bc_status ws_ext(Ctx *ctx, TileWS *ws) {
+  if (ws->ext_arrays) return BC_OK;
+  const size_t NT = (size_t)ws->n * ws->T;
+  bc_status s = ctx->mem.alloc(nullptr, NT * 12);
+  if (s) return s;
+  cudaError_t e = cudaSuccess;
+  TA(ws->xm, NT * 8);
+  TA(ws->xe, NT * 4);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (ws->xm) cudaFree(ws->xm);
+    ws->xm = nullptr;
+    ctx->mem.release(nullptr, NT * 12);
+    return fail(BC_ENOMEM, "extended-sigma arrays allocation failed");
+  }
+  ws->ext_arrays = true;
+  ws->bytes_ext = NT * 12;
+  return BC_OK;
+}
+
+static bc_status ws_A(Ctx *ctx, TileWS *ws, int64_t cap) {
+  if (ws->A && ws->capA >= cap) return BC_OK;
+  ws_release(ctx, ws, false, false, true);
+  const size_t bytes = (size_t)cap * (8 + 4 * ws->G);
+  bc_status s = ctx->mem.alloc(nullptr, bytes);
+  if (s) return s;
+  cudaError_t e = cudaSuccess;
+  TA(ws->A, (size_t)cap * 4);
+  TA(ws->ACD, (size_t)cap * 4);
+  TA(ws->AM, (size_t)cap * 4 * ws->G);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->mem.release(nullptr, bytes);
+    if (ws->A) cudaFree(ws->A);
+    if (ws->ACD) cudaFree(ws->ACD);
+    ws->A = ws->ACD = nullptr;
+    return fail(BC_ENOMEM, "tile active-list allocation failed");
+  }
+  ws->capA = cap;
+  ws->bytes_A = bytes;
+  return BC_OK;
+}
+
+static bc_status ws_lists(Ctx *ctx, TileWS *ws, const DeviceGraph *dg, cudaStream_t st) {
+  if (ws->hubs && ws->lists_for == dg->rp) return BC_OK;
+  lists_release(ctx, ws);
+  const size_t N = (size_t)dg->n;
+  const size_t bytes = N * 4 * 3 + 16;
+  bc_status s = ctx->mem.alloc(nullptr, bytes);
+  if (s) return s;
+  cudaError_t e = cudaSuccess;
+  TA(ws->hubs, N * 4);
+  TA(ws->Lbu, N * 4);
+  TA(ws->PDbu, N * 4 + 4);
+  int32_t *flag = nullptr, *pos = nullptr, *degs = nullptr;
+  int *d_cnt = nullptr;
+  void *scratch = nullptr;
+  TA(flag, (N + 1) * 4);
+  TA(pos, (N + 1) * 4);
+  TA(degs, (N + 1) * 4);
+  TA(d_cnt, 16);
+  TA(scratch, scan_scratch_bytes((int64_t)N + 1));
+  int h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 16, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, (N + 1) * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(degs, 0, (N + 1) * 4, st);
+  if (e == cudaSuccess) {
+    k_lists<<<ctx->num_sms * 4, 256, 0, st>>>(dg->n, dg->rp, ws->hubs, d_cnt, flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = scan_exclusive_i32(flag, pos, (int64_t)N + 1, scratch, st);
+  if (e == cudaSuccess) {
+    k_lists_fill<<<ctx->num_sms * 4, 256, 0, st>>>(dg->n, dg->rp, flag, pos, ws->Lbu, degs);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_cnt, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h + 1, pos + N, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  // degree prefix of the bottom-up list (degs[nbu] is 0, so PDbu[nbu] is the total)
+  if (e == cudaSuccess) e = scan_exclusive_i32(degs, ws->PDbu, (int64_t)h[1] + 1, scratch, st);
+  int ebu = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ebu, ws->PDbu + h[1], 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (flag) cudaFree(flag);
+  if (pos) cudaFree(pos);
+  if (degs) cudaFree(degs);
+  if (d_cnt) cudaFree(d_cnt);
+  if (scratch) cudaFree(scratch);
+  ws->bytes_lists = bytes;
+  if (e != cudaSuccess) {
+    lists_release(ctx, ws);
+    return cuda_fail(e, "tile vertex lists");
+  }
+  ws->nhubs = h[0];
+  ws->nbu = h[1];
+  ws->Ebu = ebu;
+  ws->lists_for = dg->rp;
+  return BC_OK;
+}
+
+static bc_status launch(void *f, dim3 grid, dim3 block, TK &p, size_t smem, cudaStream_t st) {
+  void *args[] = {&p};
+  const cudaError_t e = cudaLaunchKernel(f, grid, block, args, smem, st);
+  return e == cudaSuccess ? BC_OK : cuda_fail(e, "cudaLaunchKernel (tile phase)");
+}
+
+static bc_status capture_chunk(cudaStream_t st, cudaGraphExec_t *out, const KPtrs &k, dim3 grid,
+                               dim3 block, TK &p, bool fwd) {
+  cudaGraph_t graph;
+  BC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  bc_status s = BC_OK;
+  for (int i = 0; i < kLevelsPerChunk && !s; i++) {
+    if (fwd) {
+      s = launch(k.mark, grid, block, p, 0, st);
+      if (!s) s = launch(k.pull, grid, block, p, kSmemTile, st);
+      if (!s) s = launch((void *)k_fwd_end, dim3(1), dim3(1), p, 0, st);
+    } else {
+      s = launch(k.blevel, grid, block, p, kSmemTile, st);
+      if (!s) s = launch((void *)k_bwd_step, dim3(1), dim3(1), p, 0, st);
+    }
+  }
+  const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  if (s) return s;
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+  const cudaError_t ie = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+  return BC_OK;
+}
+
+// Run one tile (forward + backward) in loop mode `mode`; returns the device error code in
+// *derr and the number of kernel launches in *launches.
+static bc_status run_tile(Ctx *ctx, TileWS *ws, TK &p, int G, bool ext, int mode, bool fwd_only,
+                          cudaStream_t st, int *derr, int64_t *launches, int *lmax_out) {
+  const size_t N = (size_t)ws->n, NG = N * G;
+  const KPtrs k = kptrs(G, ext);
+  bc_status s = set_attrs(G, ext);
+  if (s) return s;
+  BC_CUDA_TRY(cudaMemsetAsync(ws->F, 0, NG * 4 * 3, st));
+  BC_CUDA_TRY(cudaMemsetAsync(ws->ovf, 0, NG * 4, st));
+  BC_CUDA_TRY(cudaMemsetAsync(ws->ctl, 0, sizeof(TileCtl), st));
+  const int nsm = ctx->num_sms;
+  const dim3 grid(nsm), block(k.tpb);
+  *launches = 0;
+  *derr = 0;
+  if (mode == 0) {
+    int fo = fwd_only ? 1 : 0;
+    void *args[] = {&p, &fo};
+    const cudaError_t le = cudaLaunchCooperativeKernel(k.persistent, grid, block, args, kSmemTile, st);
+    if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(tile)");
+    *launches = 1;
+  } else {
+    s = launch(k.init_vis, grid, block, p, 0, st);
+    if (!s) s = launch(k.init_src, dim3(1), dim3(1), p, 0, st);
+    if (s) return s;
+    *launches += 2;
+    cudaGraphExec_t gexec = nullptr;
+    if (mode == 2) {
+      s = capture_chunk(st, &gexec, k, grid, block, p, true);
+      if (s) return s;
+    }
+    int guard = 0;
+    for (;;) {
+      if (mode == 2) {
+        const cudaError_t ce = cudaGraphLaunch(gexec, st);
+        if (ce != cudaSuccess) {
+          cudaGraphExecDestroy(gexec);
+          return cuda_fail(ce, "cudaGraphLaunch");
+        }
+      } else {
+        for (int i = 0; i < kLevelsPerChunk && !s; i++) {
+          s = launch(k.mark, grid, block, p, 0, st);
+          if (!s) s = launch(k.pull, grid, block, p, kSmemTile, st);
+          if (!s) s = launch((void *)k_fwd_end, dim3(1), dim3(1), p, 0, st);
+        }
+        if (s) return s;
+      }
+      *launches += 3 * kLevelsPerChunk;
+      int hd[2];
+      BC_CUDA_TRY(cudaMemcpyAsync(hd, &p.ctl->bar.err, 4, cudaMemcpyDeviceToHost, st));
+      BC_CUDA_TRY(cudaMemcpyAsync(hd + 1, &p.ctl->done, 4, cudaMemcpyDeviceToHost, st));
+      BC_CUDA_TRY(cudaStreamSynchronize(st));
+      if (hd[0]) {  // device error (capacity): stop, the caller retries or fails
+        if (gexec) cudaGraphExecDestroy(gexec);
+        *derr = hd[0];
+        return BC_OK;
+      }
+      if (hd[1]) break;
+      if (++guard > ws->n / kLevelsPerChunk + 4) {  // levels <= n
+        if (gexec) cudaGraphExecDestroy(gexec);
+        return fail(BC_ECUDA, "tile level loop did not terminate");
+      }
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    int hc[2];
+    BC_CUDA_TRY(cudaMemcpyAsync(hc, &p.ctl->ovf_any, 4, cudaMemcpyDeviceToHost, st));
+    BC_CUDA_TRY(cudaMemcpyAsync(hc + 1, &p.ctl->lmax, 4, cudaMemcpyDeviceToHost, st));
+    BC_CUDA_TRY(cudaStreamSynchronize(st));
+    *lmax_out = hc[1];
+    if (fwd_only) return BC_OK;
+    if (!ext && hc[0]) {
+      *derr = BCD_NEEDEXT;
+      return BC_OK;
+    }
+    const int lmax = hc[1];
+    if (lmax >= 1) {
+      s = launch(k.bdeep, grid, block, p, 0, st);
+      if (s) return s;
+      *launches += 1;
+      const int nb = lmax - 1;  // backward levels lmax-1 .. 1
+      if (mode == 2 && nb > 0) {
+        s = capture_chunk(st, &gexec, k, grid, block, p, false);
+        if (s) return s;
+        for (int c = 0; c < (nb + kLevelsPerChunk - 1) / kLevelsPerChunk; c++) {
+          const cudaError_t le = cudaGraphLaunch(gexec, st);
+          if (le != cudaSuccess) {
+            cudaGraphExecDestroy(gexec);
+            return cuda_fail(le, "cudaGraphLaunch");
+          }
+          *launches += 2 * kLevelsPerChunk;
+        }
+        cudaGraphExecDestroy(gexec);
+      } else {
+        for (int i = 0; i < nb && !s; i++) {
+          s = launch(k.blevel, grid, block, p, kSmemTile, st);
+          if (!s) s = launch((void *)k_bwd_step, dim3(1), dim3(1), p, 0, st);
+          *launches += 2;
+        }
+        if (s) return s;
+      }
+    }
+    s = launch((void *)k_leaf, dim3(1), dim3(1), p, 0, st);
+    if (s) return s;
+    *launches += 1;
+  }
+  TileCtl h;
+  BC_CUDA_TRY(cudaMemcpyAsync(&h, ws->ctl, sizeof(TileCtl), cudaMemcpyDeviceToHost, st));
+  BC_CUDA_TRY(cudaStreamSynchronize(st));
+  *derr = h.bar.err;
+  *lmax_out = h.lmax;
+  return BC_OK;
+}
+
+bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStream_t st,
+                   bc_stats *acc) {
+  (void)g;
+  if (a.nsrc <= 0) return BC_OK;
+  if (a.T != 32 && a.T != 64 && a.T != 128 && a.T != 256)
+    return fail(BC_EINVAL, "tile width must be 32, 64, 128 or 256");
+  const DeviceGraph *dg = a.g;
+  if (!*wsp) {
+    *wsp = new (std::nothrow) TileWS();
+    if (!*wsp) return fail(BC_ENOMEM, "host allocation failed");
+  }
+  TileWS *ws = *wsp;
+  bc_status s = ws_main(ctx, ws, dg->n, a.T);
+  if (!s) s = ws_lists(ctx, ws, dg, st);
+  if (s) return s;
+  const int G = a.T / 32;
+  if (!ws->A) {
+    s = ws_A(ctx, ws, (int64_t)dg->n * 4 + 1024);
+    if (s) return s;
+  }
+  cudaEvent_t e0, e1;
+  BC_CUDA_TRY(cudaEventCreate(&e0));
+  BC_CUDA_TRY(cudaEventCreate(&e1));
+  float total_ms = 0.f;
+  int64_t launches_total = 0, levels_total = 0, ovf_sources = 0;
+  int maxd = 0;
+  for (int t0 = 0; t0 < a.nsrc && !s; t0 += a.T) {
+    const int nt = a.nsrc - t0 < a.T ? a.nsrc - t0 : a.T;
+    bool ext = ws->ext_sticky;
+    for (int attempt = 0; attempt < 24; attempt++) {
+      if (ext) {
+        s = ws_ext(ctx, ws);
+        if (s) break;
+      }
+      TK p;
+      memset(&p, 0, sizeof(p));
+      p.n = dg->n;
+      p.nnz = dg->nnz;
+      p.nsrc = nt;
+      p.rp = dg->rp;
+      p.ci = dg->ci;
+      p.omega = a.omega;
+      p.src = a.src + t0;
+      p.bc = a.bc;
+      p.leaf_term = a.omega != nullptr;
+      p.vis = ws->vis;
+      p.F = ws->F;
+      p.ovf = ws->ovf;
+      p.cand = ws->cand;
+      p.sig = ws->sig;
+      p.r = ws->r;
+      p.xm = ws->xm;
+      p.xe = ws->xe;
+      p.A = ws->A;
+      p.ACD = ws->ACD;
+      p.AM = ws->AM;
+      p.capA = ws->capA;
+      p.Aoff = ws->Aoff;
+      p.C = ws->C;
+      p.CPD = ws->CPD;
+      p.Ch = ws->Ch;
+      p.hubs = ws->hubs;
+      p.Lbu = ws->Lbu;
+      p.PDbu = ws->PDbu;
+      p.nhubs = ws->nhubs;
+      p.nbu = ws->nbu;
+      p.Ebu = ws->Ebu;
+      p.wsrc = ws->wsrc;
+      p.ctl = ws->ctl;
+      for (int gi = 0; gi < 8; gi++) {
+        uint32_t m = 0;
+        for (int b = 0; b < 32; b++)
+          if (gi * 32 + b >= nt) m |= 1u << b;
+        p.unused[gi] = m;
+      }
+      p.alpha = a.alpha;
+      p.limit_ns = ctx->wait_limit_ns;
+      k_wsrc<<<(a.T + 255) / 256, 256, 0, st>>>(p.src, nt, a.omega, ws->wsrc, a.T);
+      BC_CUDA_TRY(cudaEventRecord(e0, st));
+      int derr = 0, lmax = 0;
+      int64_t launches = 0;
+      const bool fwd_only = a.out_depth != nullptr;
+      s = run_tile(ctx, ws, p, G, ext, a.loop_mode, fwd_only, st, &derr, &launches, &lmax);
+      if (s) break;
+      BC_CUDA_TRY(cudaEventRecord(e1, st));
+      BC_CUDA_TRY(cudaEventSynchronize(e1));
+      if (derr == BCD_CAPACITY) {
+        BC_CUDA_TRY(cudaMemsetAsync(ws->cand, 0, ((size_t)ws->n / 32 + 1) * 4, st));
+        s = ws_A(ctx, ws, ws->capA * 2);
+        if (s) break;
+        continue;
+      }
+      if (derr == BCD_NEEDEXT) {
+        ext = true;
+        ws->ext_sticky = true;
+        continue;
+      }
+      if (derr == BCD_TIMEOUT) {
+        cudaMemsetAsync(ws->cand, 0, ((size_t)ws->n / 32 + 1) * 4, st);
+        cudaStreamSynchronize(st);
+        s = fail(BC_ETIMEDOUT, "tile kernel: a grid barrier wait passed its limit");
+        break;
+      }
+      if (derr != 0) {
+        s = fail(BC_ECUDA, "tile kernel reported device error " + std::to_string(derr));
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      total_ms += ms;
+      launches_total += launches;
+      TileCtl h;
+      BC_CUDA_TRY(cudaMemcpy(&h, ws->ctl, sizeof(TileCtl), cudaMemcpyDeviceToHost));
+      levels_total += h.levels;
+      for (int gi = 0; gi < G; gi++) ovf_sources += __builtin_popcount(h.ovf_lanes[gi]);
+      if (lmax > maxd) maxd = lmax;
+      if (fwd_only) {
+        void *fx = kptrs(G, false).exportk;
+        void *args[] = {&p, &lmax, (void *)&a.out_depth, (void *)&a.out_sigma, (void *)&a.out_ovf};
+        BC_CUDA_TRY(cudaMemsetAsync(a.out_depth, 0xff, (size_t)nt * ws->n * 4, st));
+        BC_CUDA_TRY(cudaMemsetAsync(a.out_sigma, 0, (size_t)nt * ws->n * 8, st));
+        BC_CUDA_TRY(cudaMemsetAsync(a.out_ovf, 0, (size_t)nt * ws->n, st));
+        BC_CUDA_TRY(cudaLaunchKernel(fx, dim3(ctx->num_sms * 4), dim3(256), args, 0, st));
+        BC_CUDA_TRY(cudaStreamSynchronize(st));
+      }
+      break;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s) return s;
+  if (acc) {
+    acc->seconds += total_ms * 1e-3;
+    acc->sources += a.nsrc;
+    acc->kernel_launches += launches_total;
+    acc->levels += levels_total;
+    acc->sigma_overflow_sources += ovf_sources;
+    if (maxd > acc->max_depth) acc->max_depth = maxd;
+    acc->tile_width = a.T;
+  }
+  return BC_OK;
+}
+
+}  // namespace bcl

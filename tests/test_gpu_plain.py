@@ -1,0 +1,174 @@
+"""Parity of the per-source CUDA path (bc_sssp, bc_exact, bc_sources with
+BC_PATH_PLAIN) against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+import paper_1602_00963_gb300 as bc
+from bcgpu import assert_bc_close, assert_sssp_equal, upload
+
+pytestmark = pytest.mark.gpu
+
+PLAIN = bc.BC_PATH_PLAIN
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = bc.bc_ctx_create(0)
+    yield c
+    bc.bc_destroy(c)
+
+
+SMALL = [
+    gg.path_graph(2), gg.path_graph(17), gg.star_graph(9), gg.complete_graph(7),
+    gg.cycle_graph(10), gg.cycle_graph(11), gg.complete_bipartite(3, 5), gg.hypercube(5),
+    gg.random_tree(40, 1), gg.gnm(50, 20, 3), gg.gnm(60, 200, 4),
+    gg.from_edge_list(8, [(0, 1), (2, 3), (3, 4)]),  # isolated vertices, K2, P3
+]
+
+
+@pytest.mark.parametrize("gi", range(len(SMALL)))
+def test_small_exact(ctx, gi):
+    g = SMALL[gi]
+    h = upload(ctx, g)
+    got, st = bc.bc_exact(h, g.n, PLAIN)
+    assert_bc_close(got, oracle.bc_exact(g), what=g.name)
+    got, _ = bc.bc_exact(h, g.n, PLAIN | bc.BC_PRUNE_DEG1)
+    assert_bc_close(got, oracle.bc_exact(g), what=g.name + " pruned")
+    bc.bc_destroy(h)
+
+
+def test_sssp_rmat(ctx):
+    g = gg.rmat(12, 16, 1)
+    h = upload(ctx, g)
+    for s in [0, 5, 77, 1000, 4095]:
+        assert_sssp_equal(bc.bc_sssp(h, g.n, s), oracle.sssp(g, s), f"rmat12 s={s}")
+    bc.bc_destroy(h)
+
+
+def test_sssp_grid_overflow(ctx):
+    """48x48 open grid: counts pass 2^64 beyond distance ~67; sigma mod 2^64 and the
+    overflow flags must match bit for bit."""
+    g = gg.grid2d(48, 48)
+    h = upload(ctx, g)
+    for s in [0, 17 * 48 + 30, 48 * 48 - 1]:
+        got = bc.bc_sssp(h, g.n, s)
+        want = oracle.sssp(g, s)
+        assert want[2].any() or s != 0
+        assert_sssp_equal(got, want, f"grid48 s={s}")
+    bc.bc_destroy(h)
+
+
+def test_sssp_ba_and_deleted_grid(ctx):
+    for g in [gg.ba_pref_attach(3000, 9), gg.grid2d(64, 64, seed=5, delete_frac=0.1)]:
+        h = upload(ctx, g)
+        rng = np.random.Generator(np.random.PCG64(1))
+        for s in rng.choice(g.n, 6, replace=False):
+            assert_sssp_equal(bc.bc_sssp(h, g.n, int(s)), oracle.sssp(g, int(s)), f"{g.name} s={s}")
+        bc.bc_destroy(h)
+
+
+def test_exact_rmat12_all_sources(ctx):
+    """R-MAT scale 12, edge factor 16, seed 1, all sources, no pruning, no batching."""
+    g = gg.rmat(12, 16, 1)
+    h = upload(ctx, g)
+    got, st = bc.bc_exact(h, g.n, PLAIN)
+    want = oracle.bc_exact(g, nthreads=8)
+    assert_bc_close(got, want, what="rmat12 exact")
+    assert st["sources"] == int((g.degrees() > 0).sum())
+    assert st["teps_sources"] == st["sources"]
+    assert st["edges"] == g.m
+    bc.bc_destroy(h)
+
+
+def test_exact_grid_extended_sigma(ctx):
+    """Grid with deletions: sigma overflows 2^64 and FP64; delta uses the extended-range
+    sigma.  All sources of a 40x40 grid (10% deleted, largest component)."""
+    g = gg.grid2d(40, 40, seed=5, delete_frac=0.1)
+    h = upload(ctx, g)
+    got, st = bc.bc_exact(h, g.n, PLAIN)
+    assert_bc_close(got, oracle.bc_exact(g, nthreads=8), what="grid40 exact")
+    bc.bc_destroy(h)
+    g = gg.grid2d(120, 120)
+    h = upload(ctx, g)
+    src = np.array([0, 119, 60 * 120 + 60, 120 * 120 - 1], np.int32)
+    got, st = bc.bc_sources(h, g.n, src, PLAIN)
+    assert st["sigma_overflow_sources"] == 4
+    assert_bc_close(got, oracle.bc(g, src), what="grid120 sources")
+    bc.bc_destroy(h)
+
+
+def test_pruned_ba(ctx):
+    g = gg.ba_pref_attach(4000, 2)
+    h = upload(ctx, g)
+    want = oracle.bc_exact(g, nthreads=8)
+    got_p, st_p = bc.bc_exact(h, g.n, PLAIN | bc.BC_PRUNE_DEG1)
+    got_u, st_u = bc.bc_exact(h, g.n, PLAIN)
+    assert_bc_close(got_p, want, what="ba pruned")
+    assert_bc_close(got_u, want, what="ba unpruned")
+    assert st_p["sources"] < st_u["sources"]
+    assert st_p["teps_sources"] == st_u["teps_sources"]
+    bc.bc_destroy(h)
+
+
+def test_device_prune_matches_oracle(ctx):
+    for g in [gg.ba_pref_attach(2000, 4), gg.rmat(10, 4, 2), SMALL[11]]:
+        h = upload(ctx, g)
+        om, rem, rrp, rci = bc.bc_prune(h, g.n, g.nnz)
+        om0, rem0, res0 = oracle.prune_deg1(g)
+        assert (om == om0).all() and (rem == rem0).all()
+        assert (rrp == res0.row_ptr).all() and (rci == res0.col_idx).all()
+        bc.bc_destroy(h)
+
+
+def test_sources_multiset_and_device_ptrs(ctx):
+    torch = pytest.importorskip("torch")
+    g = gg.rmat(10, 8, 3)
+    h = upload(ctx, g)
+    src = np.array([3, 3, 17, 500, 1023, 3], np.int32)
+    want = oracle.bc(g, src)
+    got, st = bc.bc_sources(h, g.n, src, PLAIN)
+    assert st["sources"] == 6
+    assert_bc_close(got, want, what="multiset host")
+    dsrc = torch.from_numpy(src).cuda()
+    dout = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    bc.bc_sources(h, g.n, dsrc, PLAIN, bc_out=dout)
+    assert_bc_close(dout.cpu().numpy(), want, what="multiset device")
+    bc.bc_destroy(h)
+
+
+def test_invalid_inputs(ctx):
+    bad = gg.Graph(3, np.array([0, 1, 1, 2], np.int32), np.array([1, 2], np.int32))  # not symmetric
+    with pytest.raises(bc.BCError) as e:
+        upload(ctx, bad)
+    assert e.value.status == bc.BC_EINVAL
+    loop = gg.Graph(2, np.array([0, 2, 2], np.int32), np.array([0, 1], np.int32))
+    with pytest.raises(bc.BCError):
+        upload(ctx, loop)
+    g = gg.path_graph(5)
+    h = upload(ctx, g)
+    with pytest.raises(bc.BCError) as e:
+        bc.bc_sources(h, g.n, np.array([7], np.int32), PLAIN)
+    assert e.value.status == bc.BC_EINVAL
+    with pytest.raises(bc.BCError) as e:
+        bc.bc_sources(h, g.n, np.array([1], np.int32), PLAIN | bc.BC_PRUNE_DEG1)
+    assert e.value.status == bc.BC_EINVAL
+    bc.bc_destroy(h)
+
+
+def test_wait_limit_timeout_then_recovery(ctx):
+    """A zero device-wait limit makes the first grid barrier give up: the call returns
+    BC_ETIMEDOUT (no hang, no fault) and the context stays usable."""
+    g = gg.rmat(10, 8, 5)
+    h = upload(ctx, g)
+    bc.bc_set_wait_limit_ms(ctx, 0)
+    try:
+        with pytest.raises(bc.BCError) as e:
+            bc.bc_exact(h, g.n, PLAIN)
+        assert e.value.status == bc.BC_ETIMEDOUT
+    finally:
+        bc.bc_set_wait_limit_ms(ctx, 20000)
+    got, _ = bc.bc_exact(h, g.n, PLAIN)
+    assert_bc_close(got, oracle.bc_exact(g), what="after timeout")
+    bc.bc_destroy(h)

@@ -1,0 +1,189 @@
+"""Parity of the multi-source tile path (bc_tile_sssp, and bc_exact / bc_sources with
+BC_PATH_TILED) against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+import paper_1602_00963_gb300 as bc
+from bcgpu import assert_bc_close, assert_sssp_equal, upload
+
+pytestmark = pytest.mark.gpu
+
+TILED = bc.BC_PATH_TILED
+MODES = {"persistent": 0, "launch": bc.BC_LOOP_LAUNCH, "graph": bc.BC_LOOP_GRAPH}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = bc.bc_ctx_create(0)
+    yield c
+    bc.bc_destroy(c)
+
+
+def hub_graph():
+    """A hub of degree 3000 (pulled by a whole CTA), leaves, a second hub and a sparse
+    random part linking them, so hubs are candidates in both sweep directions."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    n = 6000
+    e = [(0, i) for i in range(1, 3001)] + [(3001, i) for i in range(2500, 5200)]
+    u = rng.integers(0, n, 6000)
+    v = rng.integers(0, n, 6000)
+    e += list(zip(u.tolist(), v.tolist()))
+    return gg.from_edge_list(n, e)
+
+
+@pytest.mark.parametrize("T", [32, 64, 128, 256])
+def test_tile_sssp_rmat(ctx, T):
+    g = gg.rmat(12, 16, 1)
+    h = upload(ctx, g)
+    src = gg.sample_sources(g, T - 3, seed=T)  # ragged tile: T - 3 lanes used
+    d, s, o = bc.bc_tile_sssp(h, g.n, src, TILED | bc.BC_TILE(T))
+    for i in range(0, len(src), 7):
+        assert_sssp_equal((d[i], s[i], o[i]), oracle.sssp(g, int(src[i])), f"rmat12 T={T} lane {i}")
+    bc.bc_destroy(h)
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+def test_tile_sssp_grid_overflow(ctx, mode):
+    g = gg.grid2d(48, 48)
+    h = upload(ctx, g)
+    src = np.array([0, 100, 17 * 48 + 30, 48 * 48 - 1, 1200], np.int32)
+    d, s, o = bc.bc_tile_sssp(h, g.n, src, TILED | bc.BC_TILE(32) | MODES[mode])
+    for i, x in enumerate(src):
+        assert_sssp_equal((d[i], s[i], o[i]), oracle.sssp(g, int(x)), f"grid48 {mode} src {x}")
+    bc.bc_destroy(h)
+
+
+def test_tile_sssp_hubs(ctx):
+    g = hub_graph()
+    h = upload(ctx, g)
+    src = np.array([0, 1, 3001, 4000, 5999, 17], np.int32)
+    for T in (32, 256):
+        d, s, o = bc.bc_tile_sssp(h, g.n, src, TILED | bc.BC_TILE(T))
+        for i, x in enumerate(src):
+            assert_sssp_equal((d[i], s[i], o[i]), oracle.sssp(g, int(x)), f"hub T={T} src {x}")
+    bc.bc_destroy(h)
+
+
+SMALL = [gg.path_graph(9), gg.star_graph(40), gg.cycle_graph(33), gg.hypercube(6),
+         gg.complete_bipartite(5, 7), gg.random_tree(70, 3), gg.gnm(90, 60, 5),
+         gg.from_edge_list(8, [(0, 1), (2, 3), (3, 4)])]
+
+
+@pytest.mark.parametrize("gi", range(len(SMALL)))
+def test_tile_exact_small(ctx, gi):
+    g = SMALL[gi]
+    h = upload(ctx, g)
+    want = oracle.bc_exact(g)
+    for T in (32, 64):
+        got, st = bc.bc_exact(h, g.n, TILED | bc.BC_TILE(T))
+        assert_bc_close(got, want, what=f"{g.name} T={T}")
+        got, _ = bc.bc_exact(h, g.n, TILED | bc.BC_TILE(T) | bc.BC_PRUNE_DEG1)
+        assert_bc_close(got, want, what=f"{g.name} T={T} pruned")
+    bc.bc_destroy(h)
+
+
+@pytest.mark.parametrize("T", [32, 64, 128, 256])
+def test_tile_exact_rmat12(ctx, T):
+    """R-MAT scale 12, edge factor 16, seed 1, all sources, tiles of T."""
+    g = gg.rmat(12, 16, 1)
+    h = upload(ctx, g)
+    got, st = bc.bc_exact(h, g.n, TILED | bc.BC_TILE(T))
+    assert_bc_close(got, oracle.bc_exact(g, nthreads=8), what=f"rmat12 T={T}")
+    assert st["tile_width"] == T
+    bc.bc_destroy(h)
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+def test_tile_exact_grid_extended(ctx, mode):
+    """Open 64 x 64 grid: sigma passes 2^64 (corner to corner ~2^124); the tile reruns in
+    extended mode.  Plus a deleted-edge grid (largest component).  All three loop modes."""
+    g = gg.grid2d(64, 64)
+    h = upload(ctx, g)
+    got, st = bc.bc_exact(h, g.n, TILED | bc.BC_TILE(64) | MODES[mode])
+    assert st["sigma_overflow_sources"] > 0
+    assert_bc_close(got, oracle.bc_exact(g, nthreads=8), what=f"grid64 {mode}")
+    bc.bc_destroy(h)
+    g = gg.grid2d(40, 40, seed=5, delete_frac=0.1)
+    h = upload(ctx, g)
+    got, st = bc.bc_exact(h, g.n, TILED | bc.BC_TILE(32) | MODES[mode])
+    assert_bc_close(got, oracle.bc_exact(g, nthreads=8), what=f"grid40 deleted {mode}")
+    bc.bc_destroy(h)
+
+
+def test_tile_big_grid_sources(ctx):
+    g = gg.grid2d(160, 160, seed=7, delete_frac=0.1)
+    h = upload(ctx, g)
+    src = gg.sample_sources(g, 40, seed=6)
+    want = oracle.bc(g, src, nthreads=8)
+    for mode in MODES.values():
+        got, st = bc.bc_sources(h, g.n, src, TILED | bc.BC_TILE(32) | mode)
+        assert_bc_close(got, want, what=f"grid160 mode {mode}")
+    bc.bc_destroy(h)
+
+
+def test_tile_pruned_ba(ctx):
+    g = gg.ba_pref_attach(5000, 2)
+    h = upload(ctx, g)
+    want = oracle.bc_exact(g, nthreads=8)
+    got, _ = bc.bc_exact(h, g.n, TILED | bc.BC_TILE(128) | bc.BC_PRUNE_DEG1)
+    assert_bc_close(got, want, what="ba pruned T=128")
+    got, _ = bc.bc_exact(h, g.n, TILED | bc.BC_TILE(128))
+    assert_bc_close(got, want, what="ba unpruned T=128")
+    bc.bc_destroy(h)
+
+
+def test_tile_hubs_exact(ctx):
+    g = hub_graph()
+    h = upload(ctx, g)
+    src = np.arange(0, g.n, 37, dtype=np.int32)
+    want = oracle.bc(g, src, nthreads=8)
+    for T in (32, 256):
+        for mode in MODES.values():
+            got, _ = bc.bc_sources(h, g.n, src, TILED | bc.BC_TILE(T) | mode)
+            assert_bc_close(got, want, what=f"hubs T={T} mode={mode}")
+    bc.bc_destroy(h)
+
+
+def test_tile_duplicates_and_plain_agree(ctx):
+    g = gg.rmat(11, 8, 4)
+    h = upload(ctx, g)
+    src = np.array([5, 5, 5, 900, 17, 900] * 11, np.int32)
+    want = oracle.bc(g, src)
+    got_t, st = bc.bc_sources(h, g.n, src, TILED | bc.BC_TILE(32))
+    got_p, _ = bc.bc_sources(h, g.n, src, bc.BC_PATH_PLAIN)
+    assert st["sources"] == src.size
+    assert_bc_close(got_t, want, what="duplicates tiled")
+    assert_bc_close(got_p, want, what="duplicates plain")
+    bc.bc_destroy(h)
+
+
+def test_tile_long_path_capacity_regrowth(ctx):
+    """A path of 3000 vertices with 256 spread sources: every vertex sits at up to 256
+    different levels of the tile, far more active-list entries than the initial
+    capacity, so the tile is rerun with a larger list."""
+    g = gg.path_graph(3000)
+    h = upload(ctx, g)
+    src = np.linspace(0, 2999, 256).astype(np.int32)
+    got, st = bc.bc_sources(h, g.n, src, TILED | bc.BC_TILE(256))
+    assert_bc_close(got, oracle.bc(g, src), what="path3000 T=256")
+    d, s, o = bc.bc_tile_sssp(h, g.n, src[:5], TILED | bc.BC_TILE(32))
+    for i in range(5):
+        assert_sssp_equal((d[i], s[i], o[i]), oracle.sssp(g, int(src[i])), "path sssp")
+    bc.bc_destroy(h)
+
+
+def test_tile_timeout_then_recovery(ctx):
+    g = gg.rmat(10, 8, 9)
+    h = upload(ctx, g)
+    bc.bc_set_wait_limit_ms(ctx, 0)
+    try:
+        with pytest.raises(bc.BCError) as e:
+            bc.bc_exact(h, g.n, TILED | bc.BC_TILE(32))
+        assert e.value.status == bc.BC_ETIMEDOUT
+    finally:
+        bc.bc_set_wait_limit_ms(ctx, 20000)
+    got, _ = bc.bc_exact(h, g.n, TILED | bc.BC_TILE(32))
+    assert_bc_close(got, oracle.bc_exact(g), what="after timeout")
+    bc.bc_destroy(h)
