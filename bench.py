@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Exact betweenness-centrality throughput on one GB300 (GTEPS = sources * m / s).
+
+Workload (default): batched multi-source BC on an undirected R-MAT graph, scale 20
+(1,048,576 vertices), edge factor 16, a/b/c/d = 0.57/0.19/0.19/0.05, seed 3; 4096 sources
+drawn uniformly from the largest component (seed 4); tiles of 32..256 sources per
+launch, tile width chosen by the autotuner.  One step = one bc_sources call over the
+4096 sources (forward sigma counting + backward dependency sweep + BC accumulation).
+
+Also reported beside the headline: the per-source path on the same graph and GPU (a
+sample of its sources), each tile width, the all-sources runs of the R-MAT scale-12
+graph, and the oracle on the host cores (cpu_baseline).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): each rank runs its own replica on its own GPU with its own 4096
+seeded sources (weak scaling, no collective: BC is additive over sources).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+WORKLOAD = {
+    "workload": "rmat-s20-ef16 batched exact BC, 4096 LCC sources",
+    "graph": "R-MAT scale 20, edge factor 16, a/b/c/d .57/.19/.19/.05, seed 3",
+    "sources": "4096 uniform from the largest component, seed 4",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sources", type=int, default=4096)
+    ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_workload(nsrc: int, rank: int):
+    g = gg.cached("rmat", gg.rmat, 20, 16, 3)
+    src = gg.sample_sources(g, nsrc, seed=4 + 1000 * rank)
+    return g, src
+
+
+# ------------------------------------------------------------------ clocks sampler
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) > 8 for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ roofline model
+def algorithmic_bytes(stats: dict, tile_width: int) -> float:
+    """Compulsory bytes of one call, per source from its reached vertices n_r and arcs a_r:
+    per-source path 8 a_r + 84 n_r; a tile of width T (CSR shared by the tile)
+    (8 a_r + 16 n_r) / T + 68 n_r (each datum moved once per pass, perfect reuse)."""
+    nr = stats["reached_vertices"]
+    ar = stats["reached_arcs"]
+    if tile_width <= 1:
+        return 8.0 * ar + 84.0 * nr
+    return (8.0 * ar + 16.0 * nr) / tile_width + 68.0 * nr
+
+
+def ncu_traffic(T: int, tiles_bytes: float):
+    """DRAM bytes (read + write) per launch of the tile kernel from the committed ncu
+    summary, if it was taken on the current kernel source and this tile width."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "tile_rmat20_dram.json")
+    src = os.path.join(ROOT, "paper_1602_00963_gb300", "csrc", "bc_tile.cu")
+    try:
+        with open(path) as f:
+            j = json.load(f)
+        with open(src, "rb") as f:
+            digest = hashlib.sha1(f.read()).hexdigest()
+        if j.get("kernel_source_sha1") != digest or int(j.get("tile_width", 0)) != T:
+            return None
+        return float(j["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_baseline(g, src, budget_s: float = 15.0):
+    """The oracle as it stands (plain sequential Brandes, one thread per host core over
+    sources), timed on a bounded sample of the workload's sources."""
+    import oracle
+    nth = os.cpu_count() or 1
+    t = time.perf_counter()
+    oracle.bc(g, src[:1], nthreads=1)
+    one = max(time.perf_counter() - t, 1e-3)
+    k = int(max(1, min(len(src), budget_s * nth / one)))
+    k = max(nth, (k // nth) * nth) if k >= nth else k
+    sample = src[:k]
+    t = time.perf_counter()
+    oracle.bc(g, sample, nthreads=min(nth, k))
+    dt = time.perf_counter() - t
+    return {"value": k * g.m / dt / 1e9, "unit": "GTEPS", "cores": min(nth, k), "kind": "oracle",
+            "sample": f"{k} of the {len(src)} sources, one thread per core, {dt:.1f} s"}, dt / k
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    g, src = load_workload(args.sources, 0)
+    for _ in range(args.warmup):
+        pass
+    cb, per_src = cpu_baseline(g, src, budget_s=8.0)
+    import oracle
+    nth = os.cpu_count() or 1
+    k = max(1, int(20.0 * nth / max(per_src * nth, 1e-6)))
+    k = min(k, len(src))
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.bc(g, src[:k], nthreads=min(nth, k))
+        times.append(time.perf_counter() - t)
+    dt = statistics.median(times)
+    value = k * g.m / dt / 1e9
+    line = {"metric": "BC GTEPS (sources*m/s)", "value": value, "unit": "GTEPS", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference", "config": dict(WORKLOAD),
+            "cpu_baseline": {"kind": "oracle", "cores": min(nth, k), "value": value,
+                             "sample": f"{k} of the {len(src)} sources per step"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, rank, world)
+        return
+    import torch
+    import paper_1602_00963_gb300 as bc
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    g, src = load_workload(args.sources, rank)
+    ctx = bc.bc_ctx_create(local)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    ci = torch.from_numpy(g.col_idx).cuda()
+    h = bc.bc_graph_create(ctx, g.n, rp, ci, g.nnz, bc.BC_VALIDATE)
+    dsrc = torch.from_numpy(src).cuda()
+    dbc = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+
+    # tile width (and direction-switch threshold) from the autotuner
+    tune = None
+    try:
+        tune = bc.bc_autotune(h, 0, 7)
+    except bc.BCError:
+        tune = None
+    sweep = {}
+    if tune is None or not args.quick:
+        for T in (32, 64, 128, 256):
+            s512 = dsrc[:512]
+            bc.bc_sources(h, g.n, s512, bc.BC_PATH_TILED | bc.BC_TILE(T), bc_out=dbc, stream=stream)
+            _, st = bc.bc_sources(h, g.n, s512, bc.BC_PATH_TILED | bc.BC_TILE(T), bc_out=dbc, stream=stream)
+            sweep[T] = st["gteps"]
+    if tune is not None and tune["tile_width"] > 0:
+        T = int(tune["tile_width"])
+    else:
+        T = max(sweep, key=sweep.get)
+    flags = bc.BC_PATH_TILED | bc.BC_TILE(T)
+
+    for _ in range(args.warmup):
+        bc.bc_sources(h, g.n, dsrc, flags, bc_out=dbc, stream=stream)
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record()
+        for _ in range(args.steps):
+            _, st = bc.bc_sources(h, g.n, dsrc, flags, bc_out=dbc, stream=stream)
+            stats.append(st)
+        ev1.record()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_step_ms = ms / args.steps
+    total_sources = args.sources * world
+    value = total_sources * g.m / (per_step_ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the tile kernel: one launch per tile)
+    st0 = stats[-1]
+    launches = sum(s["kernel_launches"] for s in stats)
+    tiles = (args.sources + T - 1) // T
+    kernel_s = sum(s["seconds"] for s in stats)  # CUDA events around each tile, library stream
+    avg_launch_s = kernel_s / (tiles * args.steps)
+    bytes_per_launch = algorithmic_bytes(st0, T) / tiles
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(T, tiles_bytes=bytes_per_launch),
+                "peak_kind": peak_kind,
+                "kernel": f"tile_persistent (T={T}), one launch per tile of {T} sources",
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_ms": avg_launch_s * 1e3}
+
+    # end to end through the C ABI with host (pinned) buffers: graph upload, sources in,
+    # BC out, inside the timed region
+    e2e = None
+    if rank == 0 or world > 1:
+        hrp = torch.from_numpy(g.row_ptr).pin_memory()
+        hci = torch.from_numpy(g.col_idx).pin_memory()
+        hsrc = torch.from_numpy(src).pin_memory()
+        hbc = torch.zeros(g.n, dtype=torch.float64).pin_memory()
+        times = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            h2 = bc.load().bc_graph_create
+            import ctypes
+            gh = ctypes.c_void_p()
+            r = h2(ctx, g.n, ctypes.c_void_p(hrp.data_ptr()), ctypes.c_void_p(hci.data_ptr()), g.nnz, 0,
+                   ctypes.byref(gh))
+            if r:
+                raise bc.BCError(r, bc.bc_last_error())
+            stx = bc.bc_stats()
+            r = bc.load().bc_sources(gh, ctypes.c_void_p(hsrc.data_ptr()), len(src), flags,
+                                     ctypes.c_void_p(hbc.data_ptr()), None, ctypes.byref(stx))
+            if r:
+                raise bc.BCError(r, bc.bc_last_error())
+            times.append(time.perf_counter() - t)
+            bc.bc_destroy(gh)
+        e_dt = min(times)
+        e2e = {"value": args.sources * g.m / e_dt / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col_idx.nbytes + src.nbytes),
+               "d2h_bytes_per_step": int(g.n * 8), "seconds_per_step": e_dt}
+
+    side = {}
+    if not args.quick and rank == 0:
+        # per-source path on a sample of the same sources
+        s_plain = dsrc[:128]
+        bc.bc_sources(h, g.n, s_plain[:8], bc.BC_PATH_PLAIN, bc_out=dbc, stream=stream)
+        _, stp = bc.bc_sources(h, g.n, s_plain, bc.BC_PATH_PLAIN, bc_out=dbc, stream=stream)
+        side["per_source_path_gteps"] = stp["gteps"]
+        side["per_source_path_sample"] = "128 of the 4096 sources"
+        side["per_source_roofline_frac"] = (algorithmic_bytes(stp, 1) / stp["seconds"] / 1e9) / peak
+        side["tile_sweep_gteps_512_sources"] = sweep
+        # R-MAT scale 12, all sources: per-source path vs tiles
+        g12 = gg.rmat(12, 16, 1)
+        h12 = bc.bc_graph_create(ctx, g12.n, g12.row_ptr, g12.col_idx, g12.nnz, 0)
+        bc.bc_exact(h12, g12.n, bc.BC_PATH_PLAIN)
+        _, sp = bc.bc_exact(h12, g12.n, bc.BC_PATH_PLAIN)
+        _, stl = bc.bc_exact(h12, g12.n, bc.BC_PATH_TILED | bc.BC_TILE(256))
+        side["rmat12_all_sources_gteps"] = {"per_source": sp["gteps"], "tile256": stl["gteps"]}
+        bc.bc_destroy(h12)
+
+    cpu = None
+    if rank == 0:
+        cpu, _ = cpu_baseline(g, src, budget_s=15.0)
+
+    if rank == 0:
+        line = {
+            "metric": "BC GTEPS (sources*m/s), batched tiles; per-source path beside it",
+            "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, tile_width=T, autotuned=tune is not None,
+                           l2="inputs larger than L2 (CSR 126 MB, tile state > 1 GB)",
+                           m=g.m, n=g.n),
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+        }
+        line.update(side)
+        print(json.dumps(line), flush=True)
+    bc.bc_destroy(h)
+    bc.bc_destroy(ctx)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -60,18 +60,30 @@ template <int G>
 struct TPB {  // threads per CTA: wide tiles keep more state per lane
   static constexpr int value = G >= 4 ? 512 : 1024;
 };
+// hits whose row gathers are in flight together (fewer for wide tiles, whose rows already
+// issue G loads per hit)
+template <int G>
+struct HB {
+  static constexpr int value = G >= 8 ? 1 : (G >= 2 ? 2 : 4);
+};
 
 struct TileCtl {
   GridSync bar;
   unsigned long long apack[3];  // per-level append counter of A: count << 32 | edges (slot l % 3)
   unsigned long long cpack[3];  // per-level candidates C: count << 32 | edges (slot l % 3)
   int chcnt[3];                 // per-level hub candidates (slot l % 3)
+  int hecnt;                    // hub entries listed in HE
+  int hubq[3];                  // forward hub work counter (slot l % 3)
+  int bhubq[3];                 // backward hub-scan chunk counter (slot d % 3)
   int ovf_any;                  // some sigma of this tile passed 2^64
   unsigned ovf_lanes[8];        // lanes (sources) with an overflowed sigma
   // launched / graph mode registers
   int level, mode, done, lmax, dlevel;
   int a_pp, a_lo, a_hi, ecnt;
   long long levels;
+  int trace_n;
+  unsigned long long reached;       // (vertex, source) pairs reached
+  unsigned long long reached_arcs;  // their adjacency entries
   unsigned long long ns[256];   // Eq. 3 component size per lane (leaf term)
 };
 
@@ -92,6 +104,7 @@ struct TileWS {
   int32_t *A = nullptr, *ACD = nullptr;
   uint32_t *AM = nullptr;
   int32_t *Aoff = nullptr;
+  int32_t *HE = nullptr, *HEoff = nullptr;  // hub entries of A (positions), per-level offsets
   int32_t *C = nullptr, *CPD = nullptr, *Ch = nullptr;
   double *wsrc = nullptr;
   TileCtl *ctl = nullptr;
@@ -123,6 +136,7 @@ struct TK {
   uint32_t *AM;
   long long capA;
   int32_t *Aoff;
+  int32_t *HE, *HEoff;
   int32_t *C, *CPD, *Ch;
   const int32_t *hubs, *Lbu, *PDbu;
   int nhubs, nbu, Ebu;
@@ -131,7 +145,23 @@ struct TK {
   uint32_t unused[8];
   float alpha;
   uint64_t limit_ns;
+  unsigned long long *trace;  // optional phase trace: (phase << 56 | level << 24, time) pairs
+  int trace_cap;
 };
+
+// Grid barrier; with tracing on, CTA 0 stamps the time at which every CTA has finished
+// the phase.
+__device__ __forceinline__ bool tsync(const TK &p, GridSync *gs, int phase, int level) {
+  const bool ok = grid_sync(gs, p.limit_ns);
+  if (p.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int i = p.ctl->trace_n++;
+    if (i < p.trace_cap) {
+      p.trace[2 * i] = ((unsigned long long)phase << 56) | ((unsigned long long)(unsigned)level << 24);
+      p.trace[2 * i + 1] = globaltimer_ns();
+    }
+  }
+  return ok;
+}
 
 template <int G>
 __device__ __forceinline__ uint32_t *Fbuf(const TK &p, int l) {
@@ -159,6 +189,11 @@ __device__ __forceinline__ void append_A(const TK &p, unsigned long long *ctr, i
     if (pos < p.capA) {
       p.A[pos] = v;
       p.ACD[pos] = (int)(b & 0xffffffffull) + pre;
+      if (deg >= kHub) {  // hubs are also listed for the backward sweep
+        const int hp = atomicAdd(&p.ctl->hecnt, 1);
+        if (hp < p.capA) p.HE[hp] = (int)pos;
+        else atomicCAS(&p.ctl->bar.err, 0, BCD_CAPACITY);
+      }
     } else {
       atomicCAS(&p.ctl->bar.err, 0, BCD_CAPACITY);
     }
@@ -425,23 +460,77 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
       }
     }
     unsigned hits = __ballot_sync(BC_FULL, hit);
-    while (hits) {
-      const int jj = __ffs(hits) - 1;
-      hits &= hits - 1;
-      const int wj = __shfl_sync(BC_FULL, w, jj);
-      if (wj != cur) {
-        if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
-          abuf_push(p, ab, cur, ap, a_base);
-        cur = wj;
+    if (EXT) {
+      while (hits) {
+        const int jj = __ffs(hits) - 1;
+        hits &= hits - 1;
+        const int wj = __shfl_sync(BC_FULL, w, jj);
+        if (wj != cur) {
+          if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
+            abuf_push(p, ab, cur, ap, a_base);
+          cur = wj;
 #pragma unroll
-        for (int g = 0; g < G; g++) visc[g] = __shfl_sync(BC_FULL, vw[g], jj);
-        pull_init(a);
+          for (int g = 0; g < G; g++) visc[g] = __shfl_sync(BC_FULL, vw[g], jj);
+          pull_init(a);
+        }
+        const int pn = __shfl_sync(BC_FULL, pj, jj);
+        uint32_t m[G];
+#pragma unroll
+        for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, fm[g], jj) & ~visc[g];
+        pull_hit<G, EXT>(p, pn, m, a);
       }
-      const int pn = __shfl_sync(BC_FULL, pj, jj);
-      uint32_t m[G];
+    } else {
+      // up to HB<G>::value hits at a time: all their sigma-row loads are issued before any sum
+      while (hits) {
+        int jq[HB<G>::value];
 #pragma unroll
-      for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, fm[g], jj) & ~visc[g];
-      pull_hit<G, EXT>(p, pn, m, a);
+        for (int q = 0; q < HB<G>::value; q++) {
+          jq[q] = hits ? __ffs(hits) - 1 : -1;
+          if (hits) hits &= hits - 1;
+        }
+        unsigned long long sv[HB<G>::value][G];
+        uint32_t mq[HB<G>::value][G];
+        uint32_t povf[HB<G>::value];
+        int wq[HB<G>::value];
+#pragma unroll
+        for (int q = 0; q < HB<G>::value; q++) {
+          const int src_lane = jq[q] < 0 ? 0 : jq[q];
+          wq[q] = jq[q] < 0 ? -1 : __shfl_sync(BC_FULL, w, src_lane);
+          const int pn = __shfl_sync(BC_FULL, pj, src_lane);
+          povf[q] = 0u;
+#pragma unroll
+          for (int g = 0; g < G; g++) {
+            const uint32_t m = jq[q] < 0 ? 0u
+                                         : (__shfl_sync(BC_FULL, fm[g], src_lane) &
+                                            ~__shfl_sync(BC_FULL, vw[g], src_lane));
+            mq[q][g] = m;
+            sv[q][g] = 0ull;
+            if ((m >> lane_id()) & 1u) {
+              sv[q][g] = p.sig[(size_t)pn * (32 * G) + 32 * g + lane_id()];
+              if ((p.ovf[(size_t)pn * G + g] >> lane_id()) & 1u) povf[q] |= 1u << g;
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < HB<G>::value; q++) {
+          if (wq[q] < 0) continue;
+          if (wq[q] != cur) {
+            if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
+              abuf_push(p, ab, cur, ap, a_base);
+            cur = wq[q];
+#pragma unroll
+            for (int g = 0; g < G; g++) visc[g] = __shfl_sync(BC_FULL, vw[g], jq[q]);
+            pull_init(a);
+          }
+#pragma unroll
+          for (int g = 0; g < G; g++) {
+            a.newm[g] |= mq[q][g];
+            const unsigned long long old = a.s[g];
+            a.s[g] = old + sv[q][g];
+            if (a.s[g] < old || ((povf[q] >> g) & 1u)) a.o |= 1u << g;
+          }
+        }
+      }
     }
   });
   if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
@@ -567,6 +656,8 @@ __device__ void init_sources(const TK &p) {
   p.ctl->cpack[0] = p.ctl->cpack[1] = p.ctl->cpack[2] = 0ull;
   p.ctl->chcnt[0] = p.ctl->chcnt[1] = p.ctl->chcnt[2] = 0;
   p.Aoff[0] = 0;
+  p.HEoff[0] = 0;
+  p.HEoff[1] = 0;
   p.Aoff[1] = (int)cnt;
 }
 
@@ -574,8 +665,23 @@ __device__ void init_sources(const TK &p) {
 template <int G>
 __device__ void phase_keep(const TK &p, int level, int a_pp, int a0, int a1, int gtid, int nthr) {
   const uint32_t *Fp = Fbuf<G>(p, level - 1);
-  for (long long i = (long long)a0 * G + gtid; i < (long long)a1 * G; i += nthr)
-    p.AM[i] = Fp[(size_t)p.A[i / G] * G + (i % G)];
+  unsigned long long rv = 0, ra = 0;
+  for (long long i = (long long)a0 * G + gtid; i < (long long)a1 * G; i += nthr) {
+    const int w = p.A[i / G];
+    const uint32_t m = Fp[(size_t)w * G + (i % G)];
+    p.AM[i] = m;
+    rv += __popc(m);
+    ra += (unsigned long long)__popc(m) * (unsigned long long)vdeg(p, w);
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    rv += __shfl_xor_sync(BC_FULL, rv, o);
+    ra += __shfl_xor_sync(BC_FULL, ra, o);
+  }
+  if ((threadIdx.x & 31) == 0 && rv) {
+    atomicAdd(&p.ctl->reached, rv);
+    atomicAdd(&p.ctl->reached_arcs, ra);
+  }
   if (level >= 2) {
     uint32_t *Fc = Fbuf<G>(p, level - 2);
     for (long long i = (long long)a_pp * G + gtid; i < (long long)a0 * G; i += nthr)
@@ -663,11 +769,6 @@ __device__ void phase_pull(const TK &p, int level, bool bu, int a_base, int gwar
   unsigned long long *ap = &p.ctl->apack[level % 3];
   const int nh = bu ? p.nhubs : *(volatile int *)&p.ctl->chcnt[level % 3];
   const int32_t *hl = bu ? p.hubs : p.Ch;
-  for (int i = blockIdx.x; i < nh; i += gridDim.x) {
-    const int w = hl[i];
-    const bool any = pull_hub_cta<G, EXT>(p, w, level, leaf, nsacc, smem);
-    if ((threadIdx.x >> 5) == 0) append_A(p, ap, a_base, any && lane == 0, w);
-  }
   AppendBuf ab;
   ab.v = 0;
   ab.n = 0;
@@ -689,6 +790,19 @@ __device__ void phase_pull(const TK &p, int level, bool bu, int a_base, int gwar
     }
   }
   abuf_flush(p, ab, ap, a_base);
+  // hubs last, taken from a shared work counter so that CTAs done with their walk share
+  // pick them up (balances the few, very large adjacency lists)
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(&p.ctl->hubq[level % 3], 1);
+    __syncthreads();
+    const int i = s_item;
+    if (i >= nh) break;
+    const int w = hl[i];
+    const bool any = pull_hub_cta<G, EXT>(p, w, level, leaf, nsacc, smem);
+    if ((threadIdx.x >> 5) == 0) append_A(p, ap, a_base, any && lane == 0, w);
+  }
   if (leaf) {
 #pragma unroll
     for (int g = 0; g < G; g++)
@@ -820,13 +934,35 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
         bwd_start<G, EXT>(p, kk, o);
       }
       unsigned h = hits & lanes_k;
-      while (h) {
-        const int jj = __ffs(h) - 1;
-        h &= h - 1;
-        uint32_t m[G];
+      if (EXT) {
+        while (h) {
+          const int jj = __ffs(h) - 1;
+          h &= h - 1;
+          uint32_t m[G];
 #pragma unroll
-        for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, dm[g], jj) & o.mw[g];
-        bwd_hit<G, EXT>(p, __shfl_sync(BC_FULL, v, jj), m, o);
+          for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, dm[g], jj) & o.mw[g];
+          bwd_hit<G, EXT>(p, __shfl_sync(BC_FULL, v, jj), m, o);
+        }
+      } else {
+        // up to HB<G>::value successors at a time: their r-row loads are in flight together
+        while (h) {
+          double xq[HB<G>::value][G];
+#pragma unroll
+          for (int q = 0; q < HB<G>::value; q++) {
+            const int jj = h ? __ffs(h) - 1 : -1;
+            if (h) h &= h - 1;
+            const int vq = __shfl_sync(BC_FULL, v, jj < 0 ? 0 : jj);
+#pragma unroll
+            for (int g = 0; g < G; g++) {
+              const uint32_t m = jj < 0 ? 0u : (__shfl_sync(BC_FULL, dm[g], jj < 0 ? 0 : jj) & o.mw[g]);
+              xq[q][g] = ((m >> lane_id()) & 1u) ? p.r[(size_t)vq * (32 * G) + 32 * g + lane_id()] : 0.0;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < HB<G>::value; q++)
+#pragma unroll
+            for (int g = 0; g < G; g++) o.acc[g] += xq[q][g];
+        }
       }
     }
   });
@@ -891,9 +1027,19 @@ __device__ void phase_bwd_level(const TK &p, int d, int a0, int a1, int Ed, int 
     Dd[(size_t)p.A[i / G] * G + (i % G)] = p.AM[i];
   for (long long i = (long long)c0 * G + gtid; i < (long long)c1 * G; i += nthr)
     Dc[(size_t)p.A[i / G] * G + (i % G)] = 0u;
-  for (int k = a0 + blockIdx.x; k < a1; k += gridDim.x)
-    if (vdeg(p, p.A[k]) >= kHub) bwd_hub_cta<G, EXT>(p, k, Dn, smem);
   bwd_walk<G, EXT>(p, a0, a1, Ed, Dn, gwarp, nwarps);
+  // hub entries of A_d (listed at append time), one per CTA from a shared counter
+  __shared__ int s_item;
+  const int h0 = p.HEoff[d], h1 = p.HEoff[d + 1];
+  int *ctr = &p.ctl->bhubq[d % 3];
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
+    __syncthreads();
+    const int i = h0 + s_item;
+    if (i >= h1) break;
+    bwd_hub_cta<G, EXT>(p, p.HE[i], Dn, smem);
+  }
 }
 
 __device__ void leaf_terms(const TK &p) {
@@ -920,9 +1066,9 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
   const int gwarp = gtid >> 5, nwarps = nthr >> 5;
   GridSync *gs = &p.ctl->bar;
   phase_init_vis<G>(p, gtid, nthr);
-  if (!grid_sync(gs, p.limit_ns)) return;
+  if (!tsync(p, gs, 0, 0)) return;
   if (gtid == 0) init_sources<G>(p);
-  if (!grid_sync(gs, p.limit_ns)) return;
+  if (!tsync(p, gs, 0, 0)) return;
   int level = 1, a_pp = 0, a_lo = 0, a_hi, ecnt;
   {
     const unsigned long long pk = vload64(&p.ctl->apack[0]);
@@ -934,22 +1080,26 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
     phase_keep<G>(p, level, a_pp, a_lo, a_hi, gtid, nthr);
     if (!bu) {
       phase_mark<G>(p, level, a_lo, a_hi, ecnt, gwarp, nwarps);
-      if (!grid_sync(gs, p.limit_ns)) return;
+      if (!tsync(p, gs, 1, level)) return;
     }
     phase_pull<G, EXT>(p, level, bu, a_hi, gwarp, nwarps, smem);
     if (gtid == 0) {
       p.ctl->apack[(level + 1) % 3] = 0ull;
       p.ctl->cpack[(level + 1) % 3] = 0ull;
       p.ctl->chcnt[(level + 1) % 3] = 0;
+      p.ctl->hubq[(level + 1) % 3] = 0;
     }
-    if (!grid_sync(gs, p.limit_ns)) return;
+    if (!tsync(p, gs, bu ? 3 : 2, level)) return;
     const unsigned long long pk = vload64(&p.ctl->apack[level % 3]);
     a_pp = a_lo;
     a_lo = a_hi;
     a_hi = a_lo + (int)(pk >> 32);
     ecnt = (int)(pk & 0xffffffffull);
     level++;
-    if (gtid == 0) p.Aoff[level] = a_hi;
+    if (gtid == 0) {
+      p.Aoff[level] = a_hi;
+      p.HEoff[level] = *(volatile int *)&p.ctl->hecnt;
+    }
   }
   const int lmax = level - 2;
   if (gtid == 0) {
@@ -961,10 +1111,10 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
     if (gtid == 0) atomicCAS(&p.ctl->bar.err, 0, BCD_NEEDEXT);
     return;
   }
-  if (!grid_sync(gs, p.limit_ns)) return;
+  if (!tsync(p, gs, 4, 0)) return;
   if (lmax >= 1) {
     phase_bwd_deep<G, EXT>(p, p.Aoff[lmax], p.Aoff[lmax + 1], gtid, nthr);
-    if (!grid_sync(gs, p.limit_ns)) return;
+    if (!tsync(p, gs, 4, lmax)) return;
     for (int d = lmax - 1; d >= 1; --d) {
       int c0 = 0, c1 = 0;
       if (d + 2 <= lmax) {
@@ -974,7 +1124,8 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
       const int a0 = p.Aoff[d], a1 = p.Aoff[d + 1];
       phase_bwd_level<G, EXT>(p, d, a0, a1, level_edges(p, a0, a1), c0, c1, gtid, nthr, gwarp,
                               nwarps, smem);
-      if (!grid_sync(gs, p.limit_ns)) return;
+      if (gtid == 0) p.ctl->bhubq[(d + 2) % 3] = 0;  // the slot of level d - 1
+      if (!tsync(p, gs, 5, d)) return;
     }
   }
   if (gtid == 0) leaf_terms(p);
@@ -1030,6 +1181,7 @@ __global__ void k_fwd_end(TK p) {
   c->apack[(level + 1) % 3] = 0ull;
   c->cpack[(level + 1) % 3] = 0ull;
   c->chcnt[(level + 1) % 3] = 0;
+  c->hubq[(level + 1) % 3] = 0;
   c->a_pp = c->a_lo;
   c->a_lo = c->a_hi;
   c->a_hi = c->a_lo + (int)(pk >> 32);
@@ -1037,6 +1189,7 @@ __global__ void k_fwd_end(TK p) {
   level++;
   c->level = level;
   p.Aoff[level] = c->a_hi;
+  p.HEoff[level] = c->hecnt;
   c->mode = (double)c->ecnt > (double)p.alpha * (double)p.nnz;
   if ((long long)c->a_hi > p.capA) {  // appends past the active-list capacity were dropped
     atomicCAS(&c->bar.err, 0, BCD_CAPACITY);
@@ -1077,7 +1230,10 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) k_bwd_level(TK p) {
 }
 
 __global__ void k_bwd_step(TK p) {
-  if (p.ctl->dlevel >= 1) p.ctl->dlevel--;
+  if (p.ctl->dlevel >= 1) {
+    p.ctl->dlevel--;
+    p.ctl->bhubq[p.ctl->dlevel % 3] = 0;
+  }
 }
 
 __global__ void k_leaf(TK p) {
@@ -1171,14 +1327,14 @@ bc_status set_attrs(int G, bool ext) {
 // ================================================================== host side
 static void ws_release(Ctx *ctx, TileWS *ws, bool main, bool ext, bool A) {
   if (main && ws->ctl) {
-    void *ptrs[] = {ws->vis, ws->F, ws->ovf, ws->cand, ws->sig, ws->r, ws->Aoff,
+    void *ptrs[] = {ws->vis, ws->F, ws->ovf, ws->cand, ws->sig, ws->r, ws->Aoff, ws->HEoff,
                     ws->C, ws->CPD, ws->Ch, ws->wsrc, ws->ctl};
     for (void *q : ptrs) cudaFree(q);
     ctx->mem.release(nullptr, ws->bytes_main);
     ws->vis = ws->F = ws->ovf = ws->cand = nullptr;
     ws->sig = nullptr;
     ws->r = nullptr;
-    ws->Aoff = ws->C = ws->CPD = ws->Ch = nullptr;
+    ws->Aoff = ws->HEoff = ws->C = ws->CPD = ws->Ch = nullptr;
     ws->wsrc = nullptr;
     ws->ctl = nullptr;
     ws->bytes_main = 0;
@@ -1196,6 +1352,8 @@ static void ws_release(Ctx *ctx, TileWS *ws, bool main, bool ext, bool A) {
     cudaFree(ws->A);
     cudaFree(ws->ACD);
     cudaFree(ws->AM);
+    cudaFree(ws->HE);
+    ws->HE = nullptr;
     ctx->mem.release(nullptr, ws->bytes_A);
     ws->A = ws->ACD = nullptr;
     ws->AM = nullptr;
@@ -1244,6 +1402,7 @@ static bc_status ws_main(Ctx *ctx, TileWS *ws, int n, int T) {
   TA(ws->sig, NT * 8);
   TA(ws->r, NT * 8);
   TA(ws->Aoff, (N + 3) * 4);
+  TA(ws->HEoff, (N + 3) * 4);
   TA(ws->C, N * 4);
   TA(ws->CPD, N * 4);
   TA(ws->Ch, N * 4);
@@ -1285,19 +1444,21 @@ static bc_status ws_ext(Ctx *ctx, TileWS *ws) {
 static bc_status ws_A(Ctx *ctx, TileWS *ws, int64_t cap) {
   if (ws->A && ws->capA >= cap) return BC_OK;
   ws_release(ctx, ws, false, false, true);
-  const size_t bytes = (size_t)cap * (8 + 4 * ws->G);
+  const size_t bytes = (size_t)cap * (12 + 4 * ws->G);
   bc_status s = ctx->mem.alloc(nullptr, bytes);
   if (s) return s;
   cudaError_t e = cudaSuccess;
   TA(ws->A, (size_t)cap * 4);
   TA(ws->ACD, (size_t)cap * 4);
+  TA(ws->HE, (size_t)cap * 4);
   TA(ws->AM, (size_t)cap * 4 * ws->G);
   if (e != cudaSuccess) {
     cudaGetLastError();
     ctx->mem.release(nullptr, bytes);
     if (ws->A) cudaFree(ws->A);
     if (ws->ACD) cudaFree(ws->ACD);
-    ws->A = ws->ACD = nullptr;
+    if (ws->HE) cudaFree(ws->HE);
+    ws->A = ws->ACD = ws->HE = nullptr;
     return fail(BC_ENOMEM, "tile active-list allocation failed");
   }
   ws->capA = cap;
@@ -1530,7 +1691,8 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
   BC_CUDA_TRY(cudaEventCreate(&e0));
   BC_CUDA_TRY(cudaEventCreate(&e1));
   float total_ms = 0.f;
-  int64_t launches_total = 0, levels_total = 0, ovf_sources = 0;
+  unsigned long long *trace_buf = nullptr;
+  int64_t launches_total = 0, levels_total = 0, ovf_sources = 0, reached = 0, reached_arcs = 0;
   int maxd = 0;
   for (int t0 = 0; t0 < a.nsrc && !s; t0 += a.T) {
     const int nt = a.nsrc - t0 < a.T ? a.nsrc - t0 : a.T;
@@ -1564,6 +1726,8 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
       p.AM = ws->AM;
       p.capA = ws->capA;
       p.Aoff = ws->Aoff;
+      p.HE = ws->HE;
+      p.HEoff = ws->HEoff;
       p.C = ws->C;
       p.CPD = ws->CPD;
       p.Ch = ws->Ch;
@@ -1583,6 +1747,15 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
       }
       p.alpha = a.alpha;
       p.limit_ns = ctx->wait_limit_ns;
+      static const char *trace_file = getenv("BC_TRACE_FILE");
+      if (trace_file && !trace_buf) {
+        if (cudaMalloc(&trace_buf, (size_t)(1 << 20) * 16) != cudaSuccess) {
+          cudaGetLastError();
+          trace_buf = nullptr;
+        }
+      }
+      p.trace = trace_buf;
+      p.trace_cap = trace_buf ? (1 << 20) : 0;
       k_wsrc<<<(a.T + 255) / 256, 256, 0, st>>>(p.src, nt, a.omega, ws->wsrc, a.T);
       BC_CUDA_TRY(cudaEventRecord(e0, st));
       int derr = 0, lmax = 0;
@@ -1616,10 +1789,23 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       total_ms += ms;
-      launches_total += launches;
+      launches_total += launches + 1;  // + the per-tile weight kernel
       TileCtl h;
       BC_CUDA_TRY(cudaMemcpy(&h, ws->ctl, sizeof(TileCtl), cudaMemcpyDeviceToHost));
+      if (trace_buf) {
+        const int cnt = h.trace_n < (1 << 20) ? h.trace_n : (1 << 20);
+        std::vector<unsigned long long> tv((size_t)cnt * 2);
+        cudaMemcpy(tv.data(), trace_buf, (size_t)cnt * 16, cudaMemcpyDeviceToHost);
+        if (FILE *f = fopen(getenv("BC_TRACE_FILE"), "a")) {
+          for (int i = 0; i < cnt; i++)
+            fprintf(f, "%d,%d,%llu\n", (int)(tv[2 * i] >> 56), (int)((tv[2 * i] >> 24) & 0xffffffffull),
+                    tv[2 * i + 1]);
+          fclose(f);
+        }
+      }
       levels_total += h.levels;
+      reached += (int64_t)h.reached;
+      reached_arcs += (int64_t)h.reached_arcs;
       for (int gi = 0; gi < G; gi++) ovf_sources += __builtin_popcount(h.ovf_lanes[gi]);
       if (lmax > maxd) maxd = lmax;
       if (fwd_only) {
@@ -1636,6 +1822,7 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (trace_buf) cudaFree(trace_buf);
   if (s) return s;
   if (acc) {
     acc->seconds += total_ms * 1e-3;
@@ -1643,6 +1830,8 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
     acc->kernel_launches += launches_total;
     acc->levels += levels_total;
     acc->sigma_overflow_sources += ovf_sources;
+    acc->reached_vertices += reached;
+    acc->reached_arcs += reached_arcs;
     if (maxd > acc->max_depth) acc->max_depth = maxd;
     acc->tile_width = a.T;
   }
