@@ -181,6 +181,28 @@ void bc_last_error(char *buf, size_t len);
 /* Library version string. */
 const char *bc_version(void);
 
+/* ---- allocation-free entry point ------------------------------------------------------
+ * No counterpart in the paper: an interface addition for callers that must not allocate
+ * device memory — code running inside memory owned by another allocator (a framework's
+ * caching allocator, a fixed pool that must not fragment), latency-critical loops where
+ * cudaMalloc's implicit device synchronisation is not acceptable, or processes under a
+ * hard device-memory quota.
+ * Computes the same as bc_sources(..., BC_PATH_PLAIN | BC_DEVICE_PTRS, ...): the sum
+ * over the multiset src[k] of delta_s, on the graph given by row_ptr[n+1] / col_idx[nnz]
+ * (a symmetric CSR as for bc_graph_create; not validated here).  Every pointer is a
+ * device pointer owned by the caller; bc_out[n] is overwritten.  Working storage is one
+ * static device array of about 3.7 MB, sized for BC_NOALLOC_MAX_N vertices, that every
+ * GPU loading the library holds until the process exits; the call allocates nothing,
+ * clears that array at its start and returns when the result is complete.  Calls share
+ * the array: calls from this process are serialised, but calls whose GPU work overlaps
+ * (e.g. from several processes on one device) race.  The first call on a device looks
+ * up the array's device address with that device current: make it before any stream
+ * capture.  n > BC_NOALLOC_MAX_N returns BC_EINVAL. */
+#define BC_NOALLOC_MAX_N 65536
+bc_status bc_sources_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                             int64_t nnz, const int32_t *src, int32_t k, double *bc_out,
+                             void *cuda_stream);
+
 /* Testing hook: device-wait limit in milliseconds for bounded spins (grid barriers);
  * 0 makes every wait give up at once so the BC_ETIMEDOUT path can be exercised. */
 bc_status bc_set_wait_limit_ms(bc_ctx *ctx, int64_t ms);

@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
         "bc_stream_cancel": [vp, u64],
         "bc_destroy": [vp],
         "bc_set_wait_limit_ms": [vp, i64],
+        "bc_sources_noalloc": [i32, vp, vp, i64, vp, i32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -281,3 +282,19 @@ def bc_stream_cancel(ctx, request_id: int):
 
 def bc_destroy(handle):
     _check(load().bc_destroy(handle))
+
+
+BC_NOALLOC_MAX_N = 65536
+
+
+def bc_sources_noalloc(n: int, row_ptr, col_idx, src, bc_out, stream=None):
+    """Allocation-free variant for callers that cannot allocate device memory: all
+    arguments are CUDA tensors the caller owns (int32 CSR, int32 sources, float64 output);
+    the library works in a static device scratch array (n <= BC_NOALLOC_MAX_N)."""
+    for t in (row_ptr, col_idx, src, bc_out):
+        if not _is_cuda(t):
+            raise ValueError("bc_sources_noalloc takes CUDA tensors only")
+    _check(load().bc_sources_noalloc(int(n), _ptr(row_ptr), _ptr(col_idx), int(col_idx.numel()),
+                                     _ptr(src), int(src.numel()), _ptr(bc_out),
+                                     ctypes.c_void_p(stream) if stream else None))
+    return bc_out

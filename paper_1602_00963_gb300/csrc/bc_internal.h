@@ -151,6 +151,8 @@ struct PlainArgs {
 bc_status plain_ensure(Ctx *ctx, PlainWS *ws, int32_t n);
 void plain_free(Ctx *ctx, PlainWS *ws);
 bc_status plain_run(Ctx *ctx, PlainWS *ws, const PlainArgs &a, cudaStream_t st, bc_stats *acc);
+bc_status plain_run_view(const PlainWS &ws, const PlainArgs &a, int num_sms, uint64_t limit_ns,
+                         cudaStream_t st, int *dev_err);
 
 // ---- device 1-degree preprocessing (bc_prune.cu)
 bc_status prune_build(Ctx *ctx, Graph *g, cudaStream_t st);

@@ -27,6 +27,7 @@
 //   (updateDep), BC[w] += (omega[s] + 1) * delta[w] (Eq. 3 / Eq. 4).
 #include <climits>
 #include <cstdio>
+#include <cstring>
 
 #include "bc_internal.h"
 
@@ -629,6 +630,62 @@ bc_status plain_ensure(Ctx *ctx, PlainWS *ws, int32_t n) {
   s = plain_reset(ws, 0);
   if (s) return s;
   BC_CUDA_TRY(cudaStreamSynchronize(0));
+  return BC_OK;
+}
+
+// Launch the per-source kernel on a workspace whose arrays the caller has already laid
+// out (and cleared: depth -1; sigma, bitmaps, acc, exponents and the control block 0).
+// Allocates nothing and creates no events; waits for the kernel and reads its error word
+// into *dev_err.
+bc_status plain_run_view(const PlainWS &ws, const PlainArgs &a, int num_sms, uint64_t limit_ns,
+                         cudaStream_t st, int *dev_err) {
+  *dev_err = 0;
+  if (a.nsrc <= 0) return BC_OK;
+  if (g_blocks_per_sm < 0) {
+    BC_CUDA_TRY(cudaFuncSetAttribute(plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSmemBytes));
+    int b = 0;
+    BC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, plain_kernel, kThreads, kSmemBytes));
+    if (b < 1) return fail(BC_ECUDA, "per-source kernel does not fit on an SM");
+    g_blocks_per_sm = 1;
+  }
+  PK p;
+  memset(&p, 0, sizeof(p));
+  p.n = a.g->n;
+  p.nnz = a.g->nnz;
+  p.max_degree = a.max_degree;
+  p.rp = a.g->rp;
+  p.ci = a.g->ci;
+  p.omega = a.omega;
+  p.src = a.src;
+  p.nsrc = a.nsrc;
+  p.bc = a.bc;
+  p.leaf_term = a.leaf_term ? 1 : 0;
+  p.depth = ws.depth;
+  p.Q = ws.Q;
+  p.CD = ws.CD;
+  p.lvl_off = ws.lvl_off;
+  p.lvl_eoff = ws.lvl_eoff;
+  p.sig = ws.sig;
+  p.ovf = ws.ovf;
+  p.vis = ws.vis;
+  p.front = ws.front;
+  p.acc = ws.acc;
+  p.r = ws.r;
+  p.xm = ws.xm;
+  p.xe = ws.xe;
+  p.ctl = ws.ctl;
+  p.alpha = a.alpha;
+  p.beta = a.beta;
+  p.limit_ns = limit_ns;
+  void *args[] = {&p};
+  cudaError_t le = cudaLaunchCooperativeKernel((void *)plain_kernel, dim3(num_sms * g_blocks_per_sm),
+                                               dim3(kThreads), args, kSmemBytes, st);
+  if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(plain_kernel)");
+  int err = 0;
+  BC_CUDA_TRY(cudaMemcpyAsync(&err, &ws.ctl->bar.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  BC_CUDA_TRY(cudaStreamSynchronize(st));
+  *dev_err = err;
   return BC_OK;
 }
 
