@@ -164,6 +164,11 @@ typedef struct {
  * stream); bc_out holds the raw sum of delta_s over the drawn sources. */
 bc_status bc_stream_submit(bc_ctx *ctx, const bc_request *req, uint64_t *request_id);
 
+/* The k distinct non-isolated sources that a BC_REQ_SAMPLED request with this seed
+ * uses (SplitMix64 stream, Floyd's sampling over the non-isolated vertices in increasing
+ * id order), written to the host array src_out[k] in increasing order. */
+bc_status bc_sample_sources(bc_graph *g, int32_t k, uint64_t seed, int32_t *src_out);
+
 /* Wait up to timeout_us (0 = do not wait, <0 = forever) for a request.  Returns
  * BC_EAGAIN while it runs; BC_OK once finished (res filled, id released). */
 bc_status bc_stream_poll(bc_ctx *ctx, uint64_t request_id, int32_t timeout_us, bc_result *res);

@@ -16,7 +16,7 @@ import numpy as np
 __all__ = [
     "BCError", "load", "bc_version", "bc_last_error", "bc_ctx_create", "bc_graph_create",
     "bc_exact", "bc_sources", "bc_sssp", "bc_tile_sssp", "bc_prune", "bc_autotune",
-    "bc_stream_submit", "bc_stream_poll", "bc_stream_cancel", "bc_destroy",
+    "bc_stream_submit", "bc_stream_poll", "bc_stream_cancel", "bc_destroy", "bc_sample_sources", "bc_sources_noalloc",
     "bc_set_wait_limit_ms", "BC_OK", "BC_EINVAL", "BC_ENOMEM", "BC_EAGAIN", "BC_ETIMEDOUT",
     "BC_ECUDA", "BC_ENOTFOUND", "BC_ECANCELED", "BC_DEVICE_PTRS", "BC_VALIDATE",
     "BC_PRUNE_DEG1", "BC_PATH_PLAIN", "BC_PATH_TILED", "BC_LOOP_LAUNCH", "BC_LOOP_GRAPH",
@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH):
         "bc_destroy": [vp],
         "bc_set_wait_limit_ms": [vp, i64],
         "bc_sources_noalloc": [i32, vp, vp, i64, vp, i32, vp, vp],
+        "bc_sample_sources": [vp, i32, u64, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -265,6 +266,13 @@ def bc_stream_submit(ctx, graph, bc_out: np.ndarray, mode: int = BC_REQ_EXACT_LI
     rid = ctypes.c_uint64()
     _check(load().bc_stream_submit(ctx, ctypes.byref(req), ctypes.byref(rid)))
     return rid.value
+
+
+def bc_sample_sources(graph, k: int, seed: int):
+    """The k sources a BC_REQ_SAMPLED request with this seed uses (sorted)."""
+    out = np.empty(k, np.int32)
+    _check(load().bc_sample_sources(graph, int(k), int(seed), _ptr(out)))
+    return out
 
 
 def bc_stream_poll(ctx, request_id: int, timeout_us: int = -1):

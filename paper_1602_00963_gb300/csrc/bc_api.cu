@@ -591,6 +591,7 @@ bc_status bc_destroy(void *handle);
 namespace bcl {
 void server_stop(Ctx *c);  // bc_serve.cu
 bool server_graph_busy(Ctx *c, Graph *g);
+void server_forget_graph(Ctx *c, Graph *g);
 
 static void graph_free(Graph *g) {
   Ctx *c = g->ctx;
@@ -613,6 +614,7 @@ extern "C" bc_status bc_destroy(void *handle) {
     if (g->inflight.load() > 0 || server_graph_busy(c, g))
       return fail(BC_EAGAIN, "bc_destroy: graph has requests in flight");
     cudaSetDevice(c->device);
+    server_forget_graph(c, g);
     {
       std::lock_guard<std::mutex> lk(c->mu);
       for (size_t i = 0; i < c->graphs.size(); i++)

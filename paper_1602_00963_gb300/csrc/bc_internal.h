@@ -172,6 +172,12 @@ struct TileArgs {
   int32_t *out_depth;     // tile sssp hook: [nsrc][n]
   unsigned long long *out_sigma;
   uint8_t *out_ovf;
+  // serving: sources of several requests share a tile; lane_req[i] (device, aligned with
+  // src) is the request slot of source i, req_bc[slot] (device) its BC buffer.  A tile's
+  // lanes may only refer to slots < nreq (nreq = 0: everything goes to bc).
+  int32_t nreq;
+  const uint8_t *lane_req;
+  double *const *req_bc;
 };
 bc_status tile_run(Ctx *ctx, Graph *g, TileWS **ws, const TileArgs &a, cudaStream_t st,
                    bc_stats *acc);

@@ -145,6 +145,9 @@ struct TK {
   uint32_t unused[8];
   float alpha;
   uint64_t limit_ns;
+  int nreq;                       // > 0: lanes route BC to per-request buffers (serving)
+  const uint8_t *lane_req;        // [T] request slot of each lane
+  double *const *req_bc;          // [nreq] device BC buffers
   unsigned long long *trace;  // optional phase trace: (phase << 56 | level << 24, time) pairs
   int trace_cap;
 };
@@ -885,19 +888,35 @@ __device__ __forceinline__ void bwd_commit(const TK &p, int w, const BwdOwner<G,
   const int lane = lane_id();
   const double om = p.omega ? (double)p.omega[w] : 0.0;
   double contrib = 0.0;
+  double dl[G];
 #pragma unroll
   for (int g = 0; g < G; g++) {
+    dl[g] = 0.0;
     if ((o.mw[g] >> lane) & 1u) {
       const size_t idx = (size_t)w * (32 * G) + 32 * g + lane;
       const double delta = o.sg[g] * o.acc[g];
-      contrib += p.wsrc[32 * g + lane] * delta;
+      dl[g] = p.wsrc[32 * g + lane] * delta;
+      contrib += dl[g];
       p.r[idx] = (1.0 + delta + om) / o.sg[g];
       if (EXT) p.xe[idx] = o.ew[g];
     }
   }
+  if (p.nreq == 0) {
 #pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) contrib += __shfl_xor_sync(BC_FULL, contrib, s);
-  if (lane == 0 && contrib != 0.0) p.bc[w] += contrib;
+    for (int s = 16; s >= 1; s >>= 1) contrib += __shfl_xor_sync(BC_FULL, contrib, s);
+    if (lane == 0 && contrib != 0.0) p.bc[w] += contrib;
+    return;
+  }
+  // lanes belong to different requests (serving): one fixed-order sum per request
+  for (int q = 0; q < p.nreq; q++) {
+    double c = 0.0;
+#pragma unroll
+    for (int g = 0; g < G; g++)
+      if (((o.mw[g] >> lane) & 1u) && p.lane_req[32 * g + lane] == q) c += dl[g];
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) c += __shfl_xor_sync(BC_FULL, c, s);
+    if (lane == 0 && c != 0.0) p.req_bc[q][w] += c;
+  }
 }
 
 // Backward walk over A_d (hubs skipped): every entry is committed once, in entry order,
@@ -1746,6 +1765,9 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
         p.unused[gi] = m;
       }
       p.alpha = a.alpha;
+      p.nreq = a.nreq;
+      p.lane_req = a.lane_req ? a.lane_req + t0 : nullptr;
+      p.req_bc = a.req_bc;
       p.limit_ns = ctx->wait_limit_ns;
       static const char *trace_file = getenv("BC_TRACE_FILE");
       if (trace_file && !trace_buf) {

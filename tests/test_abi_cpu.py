@@ -1,0 +1,53 @@
+"""CPU checks of the boundary: libbc.so builds for sm_103a, loads without a GPU, and
+exports every function include/bc.h declares; host-side helpers of the bench."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "bc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:bc_status|void|const char \*)\s*(bc_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1602_00963_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for must in ["bc_ctx_create", "bc_graph_create", "bc_exact", "bc_sources", "bc_sssp",
+                 "bc_stream_submit", "bc_stream_poll", "bc_stream_cancel", "bc_destroy",
+                 "bc_autotune", "bc_prune", "bc_tile_sssp", "bc_last_error", "bc_sources_noalloc"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_function(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_error_text_without_gpu(lib):
+    lib.bc_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.bc_version()
+    buf = ctypes.create_string_buffer(256)
+    lib.bc_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.bc_destroy(None) == 1  # BC_EINVAL, no device needed
+    lib.bc_last_error(buf, ctypes.c_size_t(len(buf)))
+    assert b"bc_destroy" in buf.value
+
+
+def test_algorithmic_bytes_model():
+    import bench
+    st = {"reached_vertices": 1000, "reached_arcs": 20000}
+    assert bench.algorithmic_bytes(st, 1) == 8 * 20000 + 84 * 1000
+    assert bench.algorithmic_bytes(st, 64) == (8 * 20000 + 16 * 1000) / 64 + 68 * 1000
