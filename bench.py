@@ -200,6 +200,72 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ serving load
+def serving_pool():
+    """Resident pool: Erdos-Renyi n = 1K / 16K / 256K (average degree 8), R-MAT scale 12 /
+    16 / 20 (EF 16), grids 256^2 / 1024^2 (10% of edges deleted, largest component);
+    seeds 10..17 in that order."""
+    return [
+        ("er-1k", gg.cached("er", gg.erdos_renyi, 1 << 10, 4 << 10, 10)),
+        ("er-16k", gg.cached("er", gg.erdos_renyi, 1 << 14, 4 << 14, 11)),
+        ("er-256k", gg.cached("er", gg.erdos_renyi, 1 << 18, 4 << 18, 12)),
+        ("rmat-s12", gg.cached("rmat", gg.rmat, 12, 16, 13)),
+        ("rmat-s16", gg.cached("rmat", gg.rmat, 16, 16, 14)),
+        ("rmat-s20", gg.cached("rmat", gg.rmat, 20, 16, 15)),
+        ("grid-256", gg.cached("grid", gg.grid2d, 256, 256, 16, 0.1)),
+        ("grid-1024", gg.cached("grid", gg.grid2d, 1024, 1024, 17, 0.1)),
+    ]
+
+
+def serving_bench(bc, ctx, rates=(0.5, 1.0, 2.0), window_s=12.0, seed=100):
+    """Poisson arrivals of BC requests over the resident pool at each rate: graph uniform,
+    k = floor(exp(U(0, ln 1024))) sources, exact list or sampled with probability 1/2.
+    Reports p50 / p99 of the latency (submit -> result) and the delivered GTEPS."""
+    pool = serving_pool()
+    handles = [bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0) for _, g in pool]
+    nonisolated = [np.flatnonzero(g.degrees() > 0).astype(np.int32) for _, g in pool]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for lam in rates:
+        reqs = []
+        t0 = time.perf_counter()
+        t_next = 0.0
+        while t_next < window_s:
+            t_next += rng.exponential(1.0 / lam)
+            gi = int(rng.integers(0, len(pool)))
+            k = int(min(1024, max(1, np.floor(np.exp(rng.uniform(0.0, np.log(1024.0)))))))
+            k = min(k, nonisolated[gi].size)
+            exact = bool(rng.integers(0, 2))
+            now = time.perf_counter() - t0
+            if t_next > now:
+                time.sleep(t_next - now)
+            buf = np.zeros(pool[gi][1].n, np.float64)
+            if exact:
+                src = rng.choice(nonisolated[gi], size=k, replace=False).astype(np.int32)
+                rid = bc.bc_stream_submit(ctx, handles[gi], buf, bc.BC_REQ_EXACT_LIST, src=src)
+            else:
+                rid = bc.bc_stream_submit(ctx, handles[gi], buf, bc.BC_REQ_SAMPLED, k=k,
+                                          seed=int(rng.integers(0, 2**40)))
+            reqs.append((rid, gi, k, buf))
+        lat, edges_done = [], 0.0
+        for rid, gi, k, buf in reqs:
+            st, res = bc.bc_stream_poll(ctx, rid, -1)
+            if res["status"] != bc.BC_OK:
+                raise RuntimeError(f"serving request failed with status {res['status']}")
+            lat.append(res["latency_seconds"])
+            edges_done += k * pool[gi][1].m
+        wall = time.perf_counter() - t0
+        out.append({"lambda_per_s": lam, "requests": len(reqs),
+                    "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                    "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                    "gteps": edges_done / wall / 1e9, "wall_s": wall})
+    for h in handles:
+        bc.bc_destroy(h)
+    return {"pool": [name for name, _ in pool], "window_s": window_s, "rates": out,
+            "requests": "graph uniform; k = floor(exp(U(0, ln 1024))); exact list or sampled 1:1; "
+                        "request-stream seed 100"}
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -339,6 +405,7 @@ def main():
         _, stl = bc.bc_exact(h12, g12.n, bc.BC_PATH_TILED | bc.BC_TILE(256))
         side["rmat12_all_sources_gteps"] = {"per_source": sp["gteps"], "tile256": stl["gteps"]}
         bc.bc_destroy(h12)
+        side["serving"] = serving_bench(bc, ctx)
 
     cpu = None
     if rank == 0:
@@ -346,7 +413,7 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "BC GTEPS (sources*m/s), batched tiles; per-source path beside it",
+            "metric": "BC GTEPS (sources·m/s) batched vs per-source on 1 GB300; serving p50/p99 latency",
             "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

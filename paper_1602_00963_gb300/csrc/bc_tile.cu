@@ -74,7 +74,9 @@ struct TileCtl {
   int chcnt[3];                 // per-level hub candidates (slot l % 3)
   int hecnt;                    // hub entries listed in HE
   int hubq[3];                  // forward hub work counter (slot l % 3)
-  int bhubq[3];                 // backward hub-scan chunk counter (slot d % 3)
+  int bhubq[3];                 // backward hub work counter (slot d % 3)
+  int wq[3];                    // forward pull walk chunk counter (slot l % 3)
+  int bq[3];                    // backward walk chunk counter (slot d % 3)
   int ovf_any;                  // some sigma of this tile passed 2^64
   unsigned ovf_lanes[8];        // lanes (sources) with an overflowed sigma
   // launched / graph mode registers
@@ -275,20 +277,15 @@ __device__ __forceinline__ int find_owner(const int32_t *PD, int lo, int hi, int
 }
 
 // Walk the adjacency of list entries [i_lo, i_hi) (entry i: vertex L[i] whose edges
-// start at the level-relative prefix PD[i]; E edges in all).  The warp's slice of edges is
-// snapped to entry starts, so each entry is walked by exactly one warp.  With SKIP_HUBS,
-// entries of degree >= kHub are jumped over.  f(valid, k, w, col) is called once per
-// 32-edge step (lane = edge) with the warp converged: k = entry, w = its vertex, col =
-// position of the edge in col_idx.
+// start at the level-relative prefix PD[i]; E edges in all), restricted to the entries
+// that start inside the edge range [eb, ee): ranges are snapped to entry starts, so each
+// entry is walked by exactly one warp.  With SKIP_HUBS, entries of degree >= kHub are
+// jumped over.  f(valid, k, w, col) is called once per 32-edge step (lane = edge) with the
+// warp converged: k = entry, w = its vertex, col = position of the edge in col_idx.
 template <bool SKIP_HUBS, typename F>
-__device__ __forceinline__ void walk(const TK &p, const int32_t *L, const int32_t *PD, int i_lo,
-                                     int i_hi, int E, int gwarp, int nwarps, F &&f) {
+__device__ __forceinline__ void walk_range(const TK &p, const int32_t *L, const int32_t *PD, int i_lo,
+                                           int i_hi, int E, int eb, int ee, F &&f) {
   const int lane = lane_id();
-  if (E <= 0 || i_hi <= i_lo) return;
-  const long long per = (((long long)E + nwarps - 1) / nwarps + 31) & ~31ll;
-  const long long ebl = (long long)gwarp * per;
-  if (ebl >= E) return;
-  const int eb = (int)ebl, ee = (int)min(ebl + per, (long long)E);
   int i0 = find_owner(PD, i_lo, i_hi, eb);
   if (PD[i0] < eb) i0++;
   if (i0 >= i_hi || PD[i0] >= ee) return;
@@ -324,6 +321,32 @@ __device__ __forceinline__ void walk(const TK &p, const int32_t *L, const int32_
       base++;
       e = (base < i1) ? PD[base] : e_end;
     }
+  }
+}
+
+// The walk over all E edges in chunks: each warp starts with chunk number gwarp, further
+// chunks are claimed from a shared counter (slow chunks, with many hits, do not hold up a
+// whole static slice).  Chunks hold E / (4 * warps) edges, between 32 and kChunk, so that
+// short levels still spread over all warps.  The next chunk is claimed before the current
+// one is walked, hiding the atomic's latency.
+constexpr int kChunk = 1024;
+
+template <bool SKIP_HUBS, typename F>
+__device__ __forceinline__ void walk(const TK &p, const int32_t *L, const int32_t *PD, int i_lo,
+                                     int i_hi, int E, int gwarp, int nwarps, int *ctr, F &&f) {
+  if (E <= 0 || i_hi <= i_lo) return;
+  long long ch = ((long long)E / (4ll * nwarps) + 31) & ~31ll;
+  ch = ch < 32 ? 32 : (ch > kChunk ? kChunk : ch);
+  const long long nch = ((long long)E + ch - 1) / ch;
+  long long c = gwarp;
+  while (c < nch) {
+    int cn = 0;
+    if (nch > nwarps && lane_id() == 0) cn = atomicAdd(ctr, 1);
+    const long long next = (nch > nwarps) ? (long long)nwarps + __shfl_sync(BC_FULL, cn, 0) : nch;
+    const long long eb = c * ch;
+    const int ee = (int)min(eb + ch, (long long)E);
+    walk_range<SKIP_HUBS>(p, L, PD, i_lo, i_hi, E, (int)eb, ee, f);
+    c = next;
   }
 }
 
@@ -443,7 +466,8 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
   pull_init(a);
 #pragma unroll
   for (int g = 0; g < G; g++) visc[g] = 0u;
-  walk<false>(p, L, PD, 0, n_list, E, gwarp, nwarps, [&](bool valid, int, int w, int col) {
+  walk<false>(p, L, PD, 0, n_list, E, gwarp, nwarps, &p.ctl->wq[level % 3],
+              [&](bool valid, int, int w, int col) {
     uint32_t vw[G], fm[G];
 #pragma unroll
     for (int g = 0; g < G; g++) {
@@ -922,10 +946,11 @@ __device__ __forceinline__ void bwd_commit(const TK &p, int w, const BwdOwner<G,
 // Backward walk over A_d (hubs skipped): every entry is committed once, in entry order,
 // with the r rows of its successors summed in edge order.
 template <int G, bool EXT>
-__device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn, int gwarp, int nwarps) {
+__device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn, int gwarp,
+                         int nwarps, int *ctr) {
   int cur = -1;
   BwdOwner<G, EXT> o;
-  walk<true>(p, p.A, p.ACD, a0, a1, E, gwarp, nwarps, [&](bool valid, int k, int, int col) {
+  walk<true>(p, p.A, p.ACD, a0, a1, E, gwarp, nwarps, ctr, [&](bool valid, int k, int, int col) {
     uint32_t dm[G];
     bool hit = false;
     int v = -1;
@@ -1046,7 +1071,7 @@ __device__ void phase_bwd_level(const TK &p, int d, int a0, int a1, int Ed, int 
     Dd[(size_t)p.A[i / G] * G + (i % G)] = p.AM[i];
   for (long long i = (long long)c0 * G + gtid; i < (long long)c1 * G; i += nthr)
     Dc[(size_t)p.A[i / G] * G + (i % G)] = 0u;
-  bwd_walk<G, EXT>(p, a0, a1, Ed, Dn, gwarp, nwarps);
+  bwd_walk<G, EXT>(p, a0, a1, Ed, Dn, gwarp, nwarps, &p.ctl->bq[d % 3]);
   // hub entries of A_d (listed at append time), one per CTA from a shared counter
   __shared__ int s_item;
   const int h0 = p.HEoff[d], h1 = p.HEoff[d + 1];
@@ -1107,6 +1132,7 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
       p.ctl->cpack[(level + 1) % 3] = 0ull;
       p.ctl->chcnt[(level + 1) % 3] = 0;
       p.ctl->hubq[(level + 1) % 3] = 0;
+      p.ctl->wq[(level + 1) % 3] = 0;
     }
     if (!tsync(p, gs, bu ? 3 : 2, level)) return;
     const unsigned long long pk = vload64(&p.ctl->apack[level % 3]);
@@ -1143,7 +1169,10 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
       const int a0 = p.Aoff[d], a1 = p.Aoff[d + 1];
       phase_bwd_level<G, EXT>(p, d, a0, a1, level_edges(p, a0, a1), c0, c1, gtid, nthr, gwarp,
                               nwarps, smem);
-      if (gtid == 0) p.ctl->bhubq[(d + 2) % 3] = 0;  // the slot of level d - 1
+      if (gtid == 0) {  // the slots of level d - 1
+        p.ctl->bhubq[(d + 2) % 3] = 0;
+        p.ctl->bq[(d + 2) % 3] = 0;
+      }
       if (!tsync(p, gs, 5, d)) return;
     }
   }
@@ -1201,6 +1230,7 @@ __global__ void k_fwd_end(TK p) {
   c->cpack[(level + 1) % 3] = 0ull;
   c->chcnt[(level + 1) % 3] = 0;
   c->hubq[(level + 1) % 3] = 0;
+  c->wq[(level + 1) % 3] = 0;
   c->a_pp = c->a_lo;
   c->a_lo = c->a_hi;
   c->a_hi = c->a_lo + (int)(pk >> 32);
@@ -1252,6 +1282,7 @@ __global__ void k_bwd_step(TK p) {
   if (p.ctl->dlevel >= 1) {
     p.ctl->dlevel--;
     p.ctl->bhubq[p.ctl->dlevel % 3] = 0;
+    p.ctl->bq[p.ctl->dlevel % 3] = 0;
   }
 }
 
