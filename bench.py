@@ -49,7 +49,31 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sources", type=int, default=4096)
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--profile-case", default=None,
+                    help="run one small case for a profiler and exit: 'tile:T:K' (one bc_sources "
+                         "call of K sources in tiles of T) or 'plain:K' on the R-MAT scale-20 graph")
     return ap.parse_args()
+
+
+def profile_case(spec: str):
+    """One bc_sources call on the bench graph, for ncu captures of a single kernel."""
+    import paper_1602_00963_gb300 as bc
+    g, src = load_workload(4096, 0)
+    ctx = bc.bc_ctx_create(0)
+    h = bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0)
+    parts = spec.split(":")
+    if parts[0] == "tile":
+        T, k = int(parts[1]), int(parts[2])
+        flags = bc.BC_PATH_TILED | bc.BC_TILE(T)
+    else:
+        k = int(parts[1])
+        flags = bc.BC_PATH_PLAIN
+    _, st = bc.bc_sources(h, g.n, src[:k], flags)
+    print(json.dumps({"profile_case": spec, "seconds": st["seconds"], "gteps": st["gteps"],
+                      "kernel_launches": st["kernel_launches"],
+                      "reached_vertices": st["reached_vertices"], "reached_arcs": st["reached_arcs"]}))
+    bc.bc_destroy(h)
+    bc.bc_destroy(ctx)
 
 
 def dist_env():
@@ -270,6 +294,9 @@ def serving_bench(bc, ctx, rates=(0.5, 1.0, 2.0), window_s=12.0, seed=100):
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     if args.impl == "reference":
         if world > 1:
             import torch.distributed as dist
