@@ -83,10 +83,25 @@ def dist_env():
     return rank, world, local
 
 
+def rank_sources(g, nsrc: int, rank: int):
+    """Rank r's sources: nsrc uniform from the largest component, seed 4 + 1000 r (rank 0
+    draws the workload's own list; other ranks draw their own, so per-rank work is fixed)."""
+    return gg.sample_sources(g, nsrc, seed=4 + 1000 * rank)
+
+
 def load_workload(nsrc: int, rank: int):
     g = gg.cached("rmat", gg.rmat, 20, 16, 3)
-    src = gg.sample_sources(g, nsrc, seed=4 + 1000 * rank)
-    return g, src
+    return g, rank_sources(g, nsrc, rank)
+
+
+def max_over_ranks(x: float, dist, device="cpu") -> float:
+    """The largest of the ranks' values of x (a time): the job ends with its slowest rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ------------------------------------------------------------------ clocks sampler
@@ -290,6 +305,47 @@ def serving_bench(bc, ctx, rates=(0.5, 1.0, 2.0), window_s=12.0, seed=100):
                         "request-stream seed 100"}
 
 
+# ------------------------------------------------------------------ side configurations
+def ba_pruning_bench(bc, ctx):
+    """Leaf-rich preferential-attachment graph, n = 262144 (40% of arrivals attach once,
+    the rest 8 times), seed 2: exact BC over all sources with and without the 1-degree
+    removal (Eq. 3 / Eq. 4), tile width from the autotuner; GTEPS counts every
+    non-isolated vertex as a source and the original m in both runs."""
+    g = gg.cached("ba", gg.ba_pref_attach, 262144, 2)
+    h = bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0)
+    tune = bc.bc_autotune(h, 0, 7)
+    T = int(tune["tile_width"]) or 128
+    flags = bc.BC_PATH_TILED | bc.BC_TILE(T)
+    bc.bc_exact(h, g.n, flags | bc.BC_PRUNE_DEG1)  # warm-up (builds the residual graph)
+    pruned, stp = bc.bc_exact(h, g.n, flags | bc.BC_PRUNE_DEG1)
+    full, stf = bc.bc_exact(h, g.n, flags)
+    bc.bc_destroy(h)
+    err = np.abs(pruned - full) / np.maximum(np.abs(full), 1.0)
+    return {"n": g.n, "m": g.m, "leaves": int(np.sum(g.degrees() == 1)), "tile_width": T,
+            "pruned_gteps": stp["gteps"], "pruned_s": stp["seconds"], "pruned_sources": stp["sources"],
+            "unpruned_gteps": stf["gteps"], "unpruned_s": stf["seconds"], "unpruned_sources": stf["sources"],
+            "speedup": stf["seconds"] / stp["seconds"], "max_rel_diff": float(err.max())}
+
+
+def grid_loop_bench(bc, ctx, T: int = 64):
+    """2-D 1024 x 1024 grid, 10% of its edges deleted (seed 5), largest component; 1024
+    sources uniform from it (seed 6), tiles of T: the level loop as one persistent
+    cooperative kernel, as one launch per phase, and as CUDA-graph chunks of launches."""
+    g = gg.cached("grid", gg.grid2d, 1024, 1024, 5, 0.1)
+    src = gg.sample_sources(g, 1024, seed=6)
+    h = bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0)
+    out = {"n": g.n, "m": g.m, "sources": int(src.size), "tile_width": T}
+    modes = {"persistent": 0, "per_level_launches": bc.BC_LOOP_LAUNCH, "cuda_graph": bc.BC_LOOP_GRAPH}
+    for name, m in modes.items():
+        flags = bc.BC_PATH_TILED | bc.BC_TILE(T) | m
+        bc.bc_sources(h, g.n, src[:T], flags)
+        _, st = bc.bc_sources(h, g.n, src, flags)
+        out[name] = {"gteps": st["gteps"], "seconds": st["seconds"], "levels": st["levels"],
+                     "kernel_launches": st["kernel_launches"]}
+    bc.bc_destroy(h)
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -358,11 +414,7 @@ def main():
             stats.append(st)
         ev1.record()
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     per_step_ms = ms / args.steps
     total_sources = args.sources * world
     value = total_sources * g.m / (per_step_ms * 1e-3) / 1e9
@@ -383,36 +435,25 @@ def main():
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_ms": avg_launch_s * 1e3}
 
-    # end to end through the C ABI with host (pinned) buffers: graph upload, sources in,
-    # BC out, inside the timed region
-    e2e = None
-    if rank == 0 or world > 1:
-        hrp = torch.from_numpy(g.row_ptr).pin_memory()
-        hci = torch.from_numpy(g.col_idx).pin_memory()
-        hsrc = torch.from_numpy(src).pin_memory()
-        hbc = torch.zeros(g.n, dtype=torch.float64).pin_memory()
-        times = []
-        for _ in range(2):
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            h2 = bc.load().bc_graph_create
-            import ctypes
-            gh = ctypes.c_void_p()
-            r = h2(ctx, g.n, ctypes.c_void_p(hrp.data_ptr()), ctypes.c_void_p(hci.data_ptr()), g.nnz, 0,
-                   ctypes.byref(gh))
-            if r:
-                raise bc.BCError(r, bc.bc_last_error())
-            stx = bc.bc_stats()
-            r = bc.load().bc_sources(gh, ctypes.c_void_p(hsrc.data_ptr()), len(src), flags,
-                                     ctypes.c_void_p(hbc.data_ptr()), None, ctypes.byref(stx))
-            if r:
-                raise bc.BCError(r, bc.bc_last_error())
-            times.append(time.perf_counter() - t)
-            bc.bc_destroy(gh)
-        e_dt = min(times)
-        e2e = {"value": args.sources * g.m / e_dt / 1e9, "unit": "GTEPS",
-               "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col_idx.nbytes + src.nbytes),
-               "d2h_bytes_per_step": int(g.n * 8), "seconds_per_step": e_dt}
+    # end to end through the public API with host (pinned) buffers: graph upload, sources
+    # in, BC out, inside the timed region (numpy views of pinned tensors: no staging copy)
+    hrp = torch.from_numpy(g.row_ptr).pin_memory().numpy()
+    hci = torch.from_numpy(g.col_idx).pin_memory().numpy()
+    hsrc = torch.from_numpy(src).pin_memory().numpy()
+    hbc = torch.zeros(g.n, dtype=torch.float64).pin_memory().numpy()
+    times = []
+    for _ in range(2):
+        barrier()
+        t = time.perf_counter()
+        gh = bc.bc_graph_create(ctx, g.n, hrp, hci, g.nnz, 0)
+        bc.bc_sources(gh, g.n, hsrc, flags, bc_out=hbc)
+        times.append(time.perf_counter() - t)
+        bc.bc_destroy(gh)
+    e_dt = max_over_ranks(min(times), dist, "cuda")
+    e2e = {"value": total_sources * g.m / e_dt / 1e9, "unit": "GTEPS",
+           "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col_idx.nbytes + src.nbytes),
+           "d2h_bytes_per_step": int(g.n * 8), "seconds_per_step": e_dt,
+           "includes": "graph upload (CSR), sources, BC download; untuned thresholds"}
 
     side = {}
     if not args.quick and rank == 0:
@@ -432,6 +473,8 @@ def main():
         _, stl = bc.bc_exact(h12, g12.n, bc.BC_PATH_TILED | bc.BC_TILE(256))
         side["rmat12_all_sources_gteps"] = {"per_source": sp["gteps"], "tile256": stl["gteps"]}
         bc.bc_destroy(h12)
+        side["ba262144_all_sources"] = ba_pruning_bench(bc, ctx)
+        side["grid1024_loop_modes"] = grid_loop_bench(bc, ctx)
         side["serving"] = serving_bench(bc, ctx)
 
     cpu = None
