@@ -523,6 +523,8 @@ __global__ void __launch_bounds__(kThreads, 1) plain_kernel(PK p) {
         p.out_sigma[v] = p.sig[v];
         p.out_ovf[v] = test_bit(p.ovf, v) ? 1 : 0;
       }
+      // every vertex is exported before any is reset below
+      if (!phase_sync(p, gs, 4, 0)) return;
     } else {
       // -------------------------------------------------------------- backward
       const bool ext = *(volatile int *)&ctl->src_ovf != 0;
