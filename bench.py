@@ -56,13 +56,19 @@ def parse():
 
 
 def profile_case(spec: str):
-    """One bc_sources call on the bench graph, for ncu captures of a single kernel."""
+    """One bc_sources call, for ncu captures of a single kernel: on the R-MAT scale-20 graph
+    ('tile:T:K', 'plain:K') or on the 1024 x 1024 deleted-edge grid ('grid:T:K'; its
+    sigma needs the extended range, so the tile runs twice when it starts in 64-bit mode)."""
     import paper_1602_00963_gb300 as bc
-    g, src = load_workload(4096, 0)
+    parts = spec.split(":")
+    if parts[0] == "grid":
+        g = gg.cached("grid", gg.grid2d, 1024, 1024, 5, 0.1)
+        src = gg.sample_sources(g, 1024, seed=6)
+    else:
+        g, src = load_workload(4096, 0)
     ctx = bc.bc_ctx_create(0)
     h = bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0)
-    parts = spec.split(":")
-    if parts[0] == "tile":
+    if parts[0] in ("tile", "grid"):
         T, k = int(parts[1]), int(parts[2])
         flags = bc.BC_PATH_TILED | bc.BC_TILE(T)
     else:

@@ -106,6 +106,7 @@ struct TileWS {
   int32_t *A = nullptr, *ACD = nullptr;
   uint32_t *AM = nullptr;
   int32_t *Aoff = nullptr;
+  unsigned long long *Lbits = nullptr;
   int32_t *HE = nullptr, *HEoff = nullptr;  // hub entries of A (positions), per-level offsets
   int32_t *C = nullptr, *CPD = nullptr, *Ch = nullptr;
   double *wsrc = nullptr;
@@ -138,6 +139,7 @@ struct TK {
   uint32_t *AM;
   long long capA;
   int32_t *Aoff;
+  unsigned long long *Lbits;  // per level l: total number of sources over the entries of A_l
   int32_t *HE, *HEoff;
   int32_t *C, *CPD, *Ch;
   const int32_t *hubs, *Lbu, *PDbu;
@@ -176,6 +178,9 @@ __device__ __forceinline__ unsigned long long vload64(const unsigned long long *
   return *(const volatile unsigned long long *)a;
 }
 __device__ __forceinline__ int vdeg(const TK &p, int v) { return p.rp[v + 1] - p.rp[v]; }
+// Warp index for warp-level work, interleaved across CTAs (warp i of every CTA before warp
+// i + 1 of any), so that a level with few work units still spreads over all SMs.
+__device__ __forceinline__ int warp_rank() { return (int)((threadIdx.x >> 5) * gridDim.x + blockIdx.x); }
 
 // Warp-aggregated append of the flagged lanes' vertices to A with its packed counter.
 __device__ __forceinline__ void append_A(const TK &p, unsigned long long *ctr, int base_off,
@@ -225,29 +230,56 @@ __device__ __forceinline__ void abuf_flush(const TK &p, AppendBuf &b, unsigned l
 }
 
 // ------------------------------------------------------------------ extended sigma
+// value = m * 2^e.  Every m here is +0 or a positive normal double, so scaling and
+// normalising are integer operations on the IEEE-754 exponent field (no FP64 pipe).
 struct XS {
   double m;
   int e;
 };
+constexpr long long kMantBits = 0x000fffffffffffffll;
+__device__ __forceinline__ bool is_zero(double m) { return __double_as_longlong(m) == 0ll; }
+// m * 2^k; results below the normal range become 0 (they join sums of terms >= 2^-1 of
+// the same scale, where they are far below the FP64 rounding)
+__device__ __forceinline__ double scale2(double m, int k) {
+  const long long b = __double_as_longlong(m);
+  if (b == 0ll) return 0.0;
+  const int ne = (int)(b >> 52) + k;
+  if (ne <= 0) return 0.0;
+  return __longlong_as_double((b & kMantBits) | ((long long)ne << 52));
+}
+// sigma mod 2^64 (not overflowed) as m in [0.5, 1) and e; the mantissa keeps the top 53
+// bits (truncated: relative error < 2^-52)
 __device__ __forceinline__ XS xs_u64(unsigned long long s) {
   XS x;
-  x.m = frexp((double)s, &x.e);
+  if (!s) {
+    x.m = 0.0;
+    x.e = 0;
+    return x;
+  }
+  const int lz = __clzll((long long)s);
+  const unsigned long long t = s << lz;
+  x.m = __longlong_as_double((long long)((t >> 11) & (unsigned long long)kMantBits) | (1022ll << 52));
+  x.e = 64 - lz;
   return x;
 }
 __device__ __forceinline__ void xs_add(XS &a, XS b) {
-  if (b.m == 0.0) return;
-  if (a.m == 0.0) { a = b; return; }
+  if (is_zero(b.m)) return;
+  if (is_zero(a.m)) {
+    a = b;
+    return;
+  }
   if (b.e > a.e) {
-    a.m = ldexp(a.m, a.e - b.e) + b.m;
+    a.m = scale2(a.m, a.e - b.e) + b.m;
     a.e = b.e;
   } else {
-    a.m += ldexp(b.m, b.e - a.e);
+    a.m += scale2(b.m, b.e - a.e);
   }
 }
-__device__ __forceinline__ XS xs_norm(XS a) {
-  int de;
-  a.m = frexp(a.m, &de);
-  a.e += de;
+__device__ __forceinline__ XS xs_norm(XS a) {  // mantissa into [0.5, 1)
+  const long long b = __double_as_longlong(a.m);
+  if (b == 0ll) return a;
+  a.e += (int)(b >> 52) - 1022;
+  a.m = __longlong_as_double((b & kMantBits) | (1022ll << 52));
   return a;
 }
 __device__ __forceinline__ XS sig_xs(const TK &p, size_t idx, bool o) {
@@ -453,13 +485,58 @@ __device__ __forceinline__ bool load_vis(const TK &p, int w, uint32_t (&visw)[G]
   return full;
 }
 
+// Up to two set bits of a lane's G-word source mask (source 32 g + bit; -1 where absent).
+// Returns the number of set bits.
+template <int G>
+__device__ __forceinline__ int two_bits(const uint32_t (&b)[G], int &t0, int &t1) {
+  int n = 0;
+  t0 = t1 = -1;
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    uint32_t x = b[g];
+    n += __popc(x);
+    if (x && t0 < 0) {
+      t0 = 32 * g + __ffs(x) - 1;
+      x &= x - 1;
+    }
+    if (x && t1 < 0) t1 = 32 * g + __ffs(x) - 1;
+  }
+  return n;
+}
+
+// A hit of at most kSparse sources (typical of high-diameter graphs, where the sources
+// of a tile rarely share a level) is loaded by its own edge lane, so all such hits of a
+// 32-edge step are in flight together; the owner's lanes then take them by shuffles.
+constexpr int kSparse = 2;
+
+// One sparse forward term: source t gets sigma s (overflow flag po, extended value x).
+template <int G, bool EXT>
+__device__ __forceinline__ void pull_sparse_add(PullAcc<G, EXT> &a, int t, unsigned long long s, bool po,
+                                                XS x) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    if ((t >> 5) != g) continue;
+    a.newm[g] |= 1u << (t & 31);
+    if (lane == (t & 31)) {
+      const unsigned long long old = a.s[g];
+      a.s[g] = old + s;
+      if (a.s[g] < old || po) a.o |= 1u << g;
+      if (EXT) xs_add(a.x[g], x);
+    }
+  }
+}
+
 // Forward pull over the walk of list L: lanes test the edges' frontier masks against their
-// owner's unvisited mask, then the hits are summed owner by owner in edge order.
+// owner's unvisited mask; then, owner by owner, the sparse hits (loaded by their lanes)
+// and the other hits (sigma rows gathered by the source lanes) are summed, each set in
+// edge order.
 template <int G, bool EXT>
 __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_t *PD, int n_list,
                           int E, int gwarp, int nwarps, AppendBuf &ab, unsigned long long *ap,
                           int a_base, bool leaf, unsigned long long (&nsacc)[G]) {
   const uint32_t *Fp = Fbuf<G>(p, level - 1);
+  const int lane = lane_id();
   int cur = -1;
   uint32_t visc[G];
   PullAcc<G, EXT> a;
@@ -467,12 +544,12 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
 #pragma unroll
   for (int g = 0; g < G; g++) visc[g] = 0u;
   walk<false>(p, L, PD, 0, n_list, E, gwarp, nwarps, &p.ctl->wq[level % 3],
-              [&](bool valid, int, int w, int col) {
-    uint32_t vw[G], fm[G];
+              [&](bool valid, int k, int w, int col) {
+    uint32_t vw[G], bm[G];
 #pragma unroll
     for (int g = 0; g < G; g++) {
       vw[g] = 0xffffffffu;
-      fm[g] = 0u;
+      bm[g] = 0u;
     }
     bool full = true;
     if (valid) full = load_vis<G>(p, w, vw);
@@ -482,79 +559,125 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
       pj = p.ci[col];
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        fm[g] = Fp[(size_t)pj * G + g];
-        hit |= (fm[g] & ~vw[g]) != 0u;
+        bm[g] = Fp[(size_t)pj * G + g] & ~vw[g];
+        hit |= bm[g] != 0u;
       }
     }
-    unsigned hits = __ballot_sync(BC_FULL, hit);
-    if (EXT) {
-      while (hits) {
-        const int jj = __ffs(hits) - 1;
-        hits &= hits - 1;
-        const int wj = __shfl_sync(BC_FULL, w, jj);
-        if (wj != cur) {
-          if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
-            abuf_push(p, ab, cur, ap, a_base);
-          cur = wj;
-#pragma unroll
-          for (int g = 0; g < G; g++) visc[g] = __shfl_sync(BC_FULL, vw[g], jj);
-          pull_init(a);
-        }
-        const int pn = __shfl_sync(BC_FULL, pj, jj);
-        uint32_t m[G];
-#pragma unroll
-        for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, fm[g], jj) & ~visc[g];
-        pull_hit<G, EXT>(p, pn, m, a);
+    int t0 = -1, t1 = -1;
+    const bool sp = hit && two_bits<G>(bm, t0, t1) <= kSparse;
+    unsigned long long s0 = 0ull, s1 = 0ull;
+    bool o0 = false, o1 = false;
+    XS x0, x1;
+    x0.m = x1.m = 0.0;
+    x0.e = x1.e = 0;
+    if (sp) {
+      const size_t i0 = (size_t)pj * (32 * G) + t0;
+      s0 = p.sig[i0];
+      o0 = (p.ovf[(size_t)pj * G + (t0 >> 5)] >> (t0 & 31)) & 1u;
+      if (t1 >= 0) {
+        const size_t i1 = (size_t)pj * (32 * G) + t1;
+        s1 = p.sig[i1];
+        o1 = (p.ovf[(size_t)pj * G + (t1 >> 5)] >> (t1 & 31)) & 1u;
       }
-    } else {
-      // up to HB<G>::value hits at a time: all their sigma-row loads are issued before any sum
-      while (hits) {
-        int jq[HB<G>::value];
-#pragma unroll
-        for (int q = 0; q < HB<G>::value; q++) {
-          jq[q] = hits ? __ffs(hits) - 1 : -1;
-          if (hits) hits &= hits - 1;
+      if (EXT) {
+        if (o0) {
+          x0.m = p.xm[i0];
+          x0.e = p.xe[i0];
+        } else {
+          x0 = xs_u64(s0);
         }
-        unsigned long long sv[HB<G>::value][G];
-        uint32_t mq[HB<G>::value][G];
-        uint32_t povf[HB<G>::value];
-        int wq[HB<G>::value];
+        if (t1 >= 0) {
+          const size_t i1 = (size_t)pj * (32 * G) + t1;
+          if (o1) {
+            x1.m = p.xm[i1];
+            x1.e = p.xe[i1];
+          } else {
+            x1 = xs_u64(s1);
+          }
+        }
+      }
+    }
+    const unsigned vm = __ballot_sync(BC_FULL, valid);
+    const unsigned sps = __ballot_sync(BC_FULL, sp);
+    const unsigned dns = __ballot_sync(BC_FULL, hit && !sp);
+    if (!(sps | dns)) return;
+    const int k_lo = __shfl_sync(BC_FULL, k, __ffs(sps | dns) - 1);
+    const int k_hi = __shfl_sync(BC_FULL, k, 31 - __clz(sps | dns));
+    for (int kk = k_lo; kk <= k_hi; kk++) {
+      const unsigned lanes_k = __ballot_sync(BC_FULL, valid && k == kk) & vm;
+      unsigned hs = sps & lanes_k, hd = dns & lanes_k;
+      if (!(hs | hd)) continue;
+      const int jl = __ffs(hs | hd) - 1;
+      const int wk = __shfl_sync(BC_FULL, w, jl);
+      if (wk != cur) {
+        if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
+          abuf_push(p, ab, cur, ap, a_base);
+        cur = wk;
 #pragma unroll
-        for (int q = 0; q < HB<G>::value; q++) {
-          const int src_lane = jq[q] < 0 ? 0 : jq[q];
-          wq[q] = jq[q] < 0 ? -1 : __shfl_sync(BC_FULL, w, src_lane);
-          const int pn = __shfl_sync(BC_FULL, pj, src_lane);
-          povf[q] = 0u;
+        for (int g = 0; g < G; g++) visc[g] = __shfl_sync(BC_FULL, vw[g], jl);
+        pull_init(a);
+      }
+      while (hs) {
+        const int jj = __ffs(hs) - 1;
+        hs &= hs - 1;
+        const int u0 = __shfl_sync(BC_FULL, t0, jj), u1 = __shfl_sync(BC_FULL, t1, jj);
+        XS y0, y1;
+        y0.m = y1.m = 0.0;
+        y0.e = y1.e = 0;
+        if (EXT) {
+          y0.m = __shfl_sync(BC_FULL, x0.m, jj);
+          y0.e = __shfl_sync(BC_FULL, x0.e, jj);
+        }
+        pull_sparse_add<G, EXT>(a, u0, __shfl_sync(BC_FULL, s0, jj), __shfl_sync(BC_FULL, o0, jj), y0);
+        if (u1 >= 0) {
+          if (EXT) {
+            y1.m = __shfl_sync(BC_FULL, x1.m, jj);
+            y1.e = __shfl_sync(BC_FULL, x1.e, jj);
+          }
+          pull_sparse_add<G, EXT>(a, u1, __shfl_sync(BC_FULL, s1, jj), __shfl_sync(BC_FULL, o1, jj), y1);
+        }
+      }
+      if (EXT) {
+        while (hd) {
+          const int jj = __ffs(hd) - 1;
+          hd &= hd - 1;
+          uint32_t m[G];
 #pragma unroll
-          for (int g = 0; g < G; g++) {
-            const uint32_t m = jq[q] < 0 ? 0u
-                                         : (__shfl_sync(BC_FULL, fm[g], src_lane) &
-                                            ~__shfl_sync(BC_FULL, vw[g], src_lane));
-            mq[q][g] = m;
-            sv[q][g] = 0ull;
-            if ((m >> lane_id()) & 1u) {
-              sv[q][g] = p.sig[(size_t)pn * (32 * G) + 32 * g + lane_id()];
-              if ((p.ovf[(size_t)pn * G + g] >> lane_id()) & 1u) povf[q] |= 1u << g;
+          for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, bm[g], jj);
+          pull_hit<G, EXT>(p, __shfl_sync(BC_FULL, pj, jj), m, a);
+        }
+      } else {
+        // up to HB<G>::value hits at a time: all their sigma-row loads are issued before any sum
+        while (hd) {
+          unsigned long long sv[HB<G>::value][G];
+          uint32_t mq[HB<G>::value][G];
+          uint32_t povf[HB<G>::value];
+#pragma unroll
+          for (int q = 0; q < HB<G>::value; q++) {
+            const int jq = hd ? __ffs(hd) - 1 : -1;
+            if (hd) hd &= hd - 1;
+            const int pn = __shfl_sync(BC_FULL, pj, jq < 0 ? 0 : jq);
+            povf[q] = 0u;
+#pragma unroll
+            for (int g = 0; g < G; g++) {
+              const uint32_t m = __shfl_sync(BC_FULL, bm[g], jq < 0 ? 0 : jq);
+              mq[q][g] = jq < 0 ? 0u : m;
+              sv[q][g] = 0ull;
+              if ((mq[q][g] >> lane) & 1u) {
+                sv[q][g] = p.sig[(size_t)pn * (32 * G) + 32 * g + lane];
+                if ((p.ovf[(size_t)pn * G + g] >> lane) & 1u) povf[q] |= 1u << g;
+              }
             }
           }
-        }
 #pragma unroll
-        for (int q = 0; q < HB<G>::value; q++) {
-          if (wq[q] < 0) continue;
-          if (wq[q] != cur) {
-            if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
-              abuf_push(p, ab, cur, ap, a_base);
-            cur = wq[q];
+          for (int q = 0; q < HB<G>::value; q++) {
 #pragma unroll
-            for (int g = 0; g < G; g++) visc[g] = __shfl_sync(BC_FULL, vw[g], jq[q]);
-            pull_init(a);
-          }
-#pragma unroll
-          for (int g = 0; g < G; g++) {
-            a.newm[g] |= mq[q][g];
-            const unsigned long long old = a.s[g];
-            a.s[g] = old + sv[q][g];
-            if (a.s[g] < old || ((povf[q] >> g) & 1u)) a.o |= 1u << g;
+            for (int g = 0; g < G; g++) {
+              a.newm[g] |= mq[q][g];
+              const unsigned long long old = a.s[g];
+              a.s[g] = old + sv[q][g];
+              if (a.s[g] < old || ((povf[q] >> g) & 1u)) a.o |= 1u << g;
+            }
           }
         }
       }
@@ -646,6 +769,279 @@ __device__ bool pull_hub_cta(const TK &p, int w, int level, bool leaf,
   return any;
 }
 
+// ------------------------------------------------------------------ lane-per-entry mode
+// On high-diameter graphs the sources of a tile rarely share a level, so most entries
+// carry one source and a few edges; walked warp-wide, each such entry costs a warp-serial
+// sequence of its own.  Levels whose entries average at most two sources and 16 edges are
+// instead run one entry per lane: the lane walks the entry's adjacency alone (four edges
+// per round, their loads in flight together), keeping the sums of two sources at a time in
+// registers (one pass per pair).  Entries with more than kLaneSrc sources or kLaneDeg
+// edges fall back to the warp-wide path, one at a time; hubs stay with whole CTAs.  Each
+// (entry, source) sum runs in edge order, so the results stay deterministic.
+constexpr int kLaneDeg = 64;
+constexpr int kLaneSrc = 8;  // sources per lane-mode entry (in passes of two)
+
+__device__ __forceinline__ bool lane_level(unsigned long long bits, long long entries, long long edges) {
+  return entries > 0 && bits <= 2ull * (unsigned long long)entries && edges <= 16ll * entries;
+}
+
+template <bool EXT>
+struct LaneSlot {
+  int t;                  // source lane of the tile, -1 while free
+  bool o;                 // sigma passed 2^64 (carry or an overflowed parent)
+  unsigned long long s;   // sigma mod 2^64
+  XS x;                   // extended sigma (EXT)
+};
+
+template <bool EXT>
+__device__ __forceinline__ void slot_init(LaneSlot<EXT> &z) {
+  z.t = -1;
+  z.o = false;
+  z.s = 0ull;
+  z.x.m = 0.0;
+  z.x.e = 0;
+}
+
+template <bool EXT>
+__device__ __forceinline__ void slot_add(LaneSlot<EXT> &z, int t, unsigned long long v, bool po, const XS &x) {
+  z.t = t;
+  const unsigned long long old = z.s;
+  z.s = old + v;
+  z.o = z.o || z.s < old || po;
+  if (EXT) xs_add(z.x, x);
+}
+
+// Sum sigma over the parents of candidate w (frontier neighbours, per unvisited source)
+// for the first two sources met; the other sources that reach w are collected in more.
+template <int G, bool EXT>
+__device__ __forceinline__ void lane_pull(const TK &p, const uint32_t *Fp, int w, const uint32_t (&vw)[G],
+                                          LaneSlot<EXT> &a, LaneSlot<EXT> &b, uint32_t (&more)[G]) {
+  const int e1 = p.rp[w + 1];
+  for (int e = p.rp[w]; e < e1; e += 4) {
+    int pj[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) pj[u] = e + u < e1 ? p.ci[e + u] : -1;
+    uint32_t fm[4][G];
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+      for (int g = 0; g < G; g++) fm[u][g] = pj[u] >= 0 ? (Fp[(size_t)pj[u] * G + g] & ~vw[g]) : 0u;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        uint32_t m = fm[u][g];
+        while (m) {
+          const int bit = __ffs(m) - 1;
+          m &= m - 1;
+          const int t = 32 * g + bit;
+          const size_t idx = (size_t)pj[u] * (32 * G) + t;
+          const unsigned long long v = p.sig[idx];
+          const bool po = (p.ovf[(size_t)pj[u] * G + g] >> bit) & 1u;
+          XS x;
+          x.m = 0.0;
+          x.e = 0;
+          if (EXT) {
+            if (po) {
+              x.m = p.xm[idx];
+              x.e = p.xe[idx];
+            } else {
+              x = xs_u64(v);
+            }
+          }
+          if (a.t < 0 || a.t == t) {
+            slot_add<EXT>(a, t, v, po, x);
+          } else if (b.t < 0 || b.t == t) {
+            slot_add<EXT>(b, t, v, po, x);
+          } else {
+            more[g] |= 1u << bit;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Add sigma of the parents of w for the known sources of slots a and b (t >= 0 or -1).
+template <int G, bool EXT>
+__device__ __forceinline__ void lane_pull_pair(const TK &p, const uint32_t *Fp, int w, LaneSlot<EXT> &a,
+                                               LaneSlot<EXT> &b) {
+  const int e1 = p.rp[w + 1];
+  const int ga = a.t >> 5, gb = b.t >= 0 ? b.t >> 5 : ga;
+  for (int e = p.rp[w]; e < e1; e += 4) {
+    int pj[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) pj[u] = e + u < e1 ? p.ci[e + u] : -1;
+    uint32_t fa[4], fb[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      fa[u] = pj[u] >= 0 ? Fp[(size_t)pj[u] * G + ga] : 0u;
+      fb[u] = (pj[u] >= 0 && b.t >= 0) ? (gb == ga ? fa[u] : Fp[(size_t)pj[u] * G + gb]) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+#pragma unroll
+      for (int z = 0; z < 2; z++) {
+        LaneSlot<EXT> &sl = z ? b : a;
+        const uint32_t f = z ? fb[u] : fa[u];
+        if (sl.t < 0 || !((f >> (sl.t & 31)) & 1u)) continue;
+        const size_t idx = (size_t)pj[u] * (32 * G) + sl.t;
+        const unsigned long long v = p.sig[idx];
+        const bool po = (p.ovf[(size_t)pj[u] * G + (sl.t >> 5)] >> (sl.t & 31)) & 1u;
+        XS x;
+        x.m = 0.0;
+        x.e = 0;
+        if (EXT) {
+          if (po) {
+            x.m = p.xm[idx];
+            x.e = p.xe[idx];
+          } else {
+            x = xs_u64(v);
+          }
+        }
+        slot_add<EXT>(sl, sl.t, v, po, x);
+      }
+    }
+  }
+}
+
+// Store one slot of a lane-mode candidate: sigma (and its extended form) and the slot's
+// bit in the new-level and overflow masks.
+template <int G, bool EXT>
+__device__ __forceinline__ void lane_store_slot(const TK &p, int w, const LaneSlot<EXT> &z, uint32_t (&nm)[G],
+                                                uint32_t (&om)[G], bool leaf) {
+  if (z.t < 0) return;
+  const size_t idx = (size_t)w * (32 * G) + z.t;
+  p.sig[idx] = z.s;
+  if (EXT && z.o) {
+    const XS x = xs_norm(z.x);
+    p.xm[idx] = x.m;
+    p.xe[idx] = x.e;
+  }
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    if ((z.t >> 5) != g) continue;
+    nm[g] |= 1u << (z.t & 31);
+    if (z.o) om[g] |= 1u << (z.t & 31);
+  }
+  if (leaf) atomicAdd(&p.ctl->ns[z.t], 1ull + (unsigned long long)p.omega[w]);
+}
+
+// Warp-wide pull of one candidate (sigma rows gathered by the source lanes).  Returns
+// whether any source reached w.
+template <int G, bool EXT>
+__device__ bool warp_pull_one(const TK &p, int level, int w, const uint32_t (&visc)[G], bool leaf,
+                              unsigned long long (&nsacc)[G]) {
+  const uint32_t *Fp = Fbuf<G>(p, level - 1);
+  PullAcc<G, EXT> a;
+  pull_init(a);
+  const int e1 = p.rp[w + 1];
+  for (int base = p.rp[w]; base < e1; base += 32) {
+    const int e = base + lane_id();
+    const int pj = e < e1 ? p.ci[e] : -1;
+    uint32_t fm[G];
+    bool hit = false;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      fm[g] = pj >= 0 ? (Fp[(size_t)pj * G + g] & ~visc[g]) : 0u;
+      hit |= fm[g] != 0u;
+    }
+    unsigned hits = __ballot_sync(BC_FULL, hit);
+    while (hits) {
+      const int jj = __ffs(hits) - 1;
+      hits &= hits - 1;
+      uint32_t m[G];
+#pragma unroll
+      for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, fm[g], jj);
+      pull_hit<G, EXT>(p, __shfl_sync(BC_FULL, pj, jj), m, a);
+    }
+  }
+  return pull_commit<G, EXT>(p, w, level, a, visc, leaf, nsacc);
+}
+
+// Lane-mode pull over the candidates C[0, nc): warps take 32 consecutive candidates.
+template <int G, bool EXT>
+__device__ void pull_lanes(const TK &p, int level, int nc, int gwarp, int nwarps, unsigned long long *ap,
+                           int a_base, bool leaf, unsigned long long (&nsacc)[G]) {
+  const uint32_t *Fp = Fbuf<G>(p, level - 1);
+  uint32_t *Fn = Fbuf<G>(p, level);
+  const int lane = lane_id();
+  for (int base = gwarp * 32; base < nc; base += nwarps * 32) {
+    const int i = base + lane;
+    const bool in = i < nc;
+    const int w = in ? p.C[i] : 0;
+    uint32_t vw[G];
+    bool full = true;
+    if (in) full = load_vis<G>(p, w, vw);
+    const bool small = in && !full && vdeg(p, w) <= kLaneDeg;
+    LaneSlot<EXT> a, b;
+    slot_init<EXT>(a);
+    slot_init<EXT>(b);
+    uint32_t more[G];
+    int nmore = 0;
+#pragma unroll
+    for (int g = 0; g < G; g++) more[g] = 0u;
+    if (small) {
+      lane_pull<G, EXT>(p, Fp, w, vw, a, b, more);
+#pragma unroll
+      for (int g = 0; g < G; g++) nmore += __popc(more[g]);
+    }
+    const bool ok = small && nmore <= kLaneSrc - 2;
+    const bool fb = in && !full && !ok;
+    const bool got = ok && a.t >= 0;
+    uint32_t nm[G], om[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) nm[g] = om[g] = 0u;
+    if (got) {
+      lane_store_slot<G, EXT>(p, w, a, nm, om, leaf);
+      lane_store_slot<G, EXT>(p, w, b, nm, om, leaf);
+      for (;;) {  // the other sources, two per pass
+        int t0, t1;
+        if (two_bits<G>(more, t0, t1) == 0) break;
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+          if ((t0 >> 5) == g) more[g] &= ~(1u << (t0 & 31));
+          if (t1 >= 0 && (t1 >> 5) == g) more[g] &= ~(1u << (t1 & 31));
+        }
+        slot_init<EXT>(a);
+        slot_init<EXT>(b);
+        a.t = t0;
+        b.t = t1;
+        lane_pull_pair<G, EXT>(p, Fp, w, a, b);
+        lane_store_slot<G, EXT>(p, w, a, nm, om, leaf);
+        lane_store_slot<G, EXT>(p, w, b, nm, om, leaf);
+      }
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        if (!nm[g]) continue;
+        p.vis[(size_t)w * G + g] = vw[g] | nm[g];
+        Fn[(size_t)w * G + g] = nm[g];
+        if (om[g]) p.ovf[(size_t)w * G + g] |= om[g];
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      const uint32_t ob = __reduce_or_sync(BC_FULL, om[g]);
+      if (lane == 0 && ob) {
+        p.ctl->ovf_any = 1;
+        atomicOr(&p.ctl->ovf_lanes[g], ob);
+      }
+    }
+    append_A(p, ap, a_base, got, w);
+    unsigned fbm = __ballot_sync(BC_FULL, fb);
+    while (fbm) {
+      const int j = __ffs(fbm) - 1;
+      fbm &= fbm - 1;
+      const int wf = __shfl_sync(BC_FULL, w, j);
+      uint32_t visc[G];
+#pragma unroll
+      for (int g = 0; g < G; g++) visc[g] = __shfl_sync(BC_FULL, vw[g], j);
+      const bool any = warp_pull_one<G, EXT>(p, level, wf, visc, leaf, nsacc);
+      append_A(p, ap, a_base, any && lane == 0, wf);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ forward phases
 template <int G>
 __device__ void phase_init_vis(const TK &p, int gtid, int nthr) {
@@ -683,6 +1079,7 @@ __device__ void init_sources(const TK &p) {
   p.ctl->cpack[0] = p.ctl->cpack[1] = p.ctl->cpack[2] = 0ull;
   p.ctl->chcnt[0] = p.ctl->chcnt[1] = p.ctl->chcnt[2] = 0;
   p.Aoff[0] = 0;
+  p.Lbits[0] = 0ull;
   p.HEoff[0] = 0;
   p.HEoff[1] = 0;
   p.Aoff[1] = (int)cnt;
@@ -708,6 +1105,7 @@ __device__ void phase_keep(const TK &p, int level, int a_pp, int a0, int a1, int
   if ((threadIdx.x & 31) == 0 && rv) {
     atomicAdd(&p.ctl->reached, rv);
     atomicAdd(&p.ctl->reached_arcs, ra);
+    atomicAdd(&p.Lbits[level - 1], rv);
   }
   if (level >= 2) {
     uint32_t *Fc = Fbuf<G>(p, level - 2);
@@ -786,7 +1184,7 @@ __device__ void phase_mark(const TK &p, int level, int a0, int a1, int E1, int g
 // Pull of level l: hubs (Ch, or every hub in bottom-up mode) by whole CTAs, then the walk
 // over C (top-down) or over every non-hub vertex (bottom-up).  Reached vertices go to A_l.
 template <int G, bool EXT>
-__device__ void phase_pull(const TK &p, int level, bool bu, int a_base, int gwarp, int nwarps,
+__device__ void phase_pull(const TK &p, int level, bool bu, int a_lo, int a_base, int gwarp, int nwarps,
                            unsigned char *smem) {
   const int lane = lane_id();
   const bool leaf = p.leaf_term && p.omega;
@@ -804,8 +1202,13 @@ __device__ void phase_pull(const TK &p, int level, bool bu, int a_base, int gwar
   } else {
     const unsigned long long cpk = vload64(&p.ctl->cpack[level % 3]);
     const int nc = (int)(cpk >> 32);
-    pull_walk<G, EXT>(p, level, p.C, p.CPD, nc, (int)(cpk & 0xffffffffull), gwarp, nwarps, ab, ap,
-                      a_base, leaf, nsacc);
+    const int ec = (int)(cpk & 0xffffffffull);
+    // lane mode: A_{l-1} (entries a_lo .. a_base) carries <= 2 sources per entry on average
+    // and the candidates have few edges
+    if (lane_level(vload64(&p.Lbits[level - 1]), a_base - a_lo, (long long)ec) && ec <= 16ll * nc)
+      pull_lanes<G, EXT>(p, level, nc, gwarp, nwarps, ap, a_base, leaf, nsacc);
+    else
+      pull_walk<G, EXT>(p, level, p.C, p.CPD, nc, ec, gwarp, nwarps, ab, ap, a_base, leaf, nsacc);
     // clear the candidate bits of this level (C and Ch)
     for (int i = gwarp * 32 + lane; i < nc; i += nwarps * 32) {
       const int w = p.C[i];
@@ -901,7 +1304,7 @@ __device__ __forceinline__ void bwd_hit(const TK &p, int v, const uint32_t (&m)[
     if ((m[g] >> lane) & 1u) {
       const size_t idx = (size_t)v * (32 * G) + 32 * g + lane;
       double x = p.r[idx];
-      if (EXT) x = ldexp(x, o.ew[g] - p.xe[idx]);
+      if (EXT) x = scale2(x, o.ew[g] - p.xe[idx]);
       o.acc[g] += x;
     }
   }
@@ -926,9 +1329,16 @@ __device__ __forceinline__ void bwd_commit(const TK &p, int w, const BwdOwner<G,
     }
   }
   if (p.nreq == 0) {
+    unsigned act = 0u;
+#pragma unroll
+    for (int g = 0; g < G; g++) act |= o.mw[g];
+    if (__popc(act) == 1) {  // one lane holds the whole sum (the reduction would add zeros)
+      if (lane == __ffs(act) - 1 && !is_zero(contrib)) p.bc[w] += contrib;
+      return;
+    }
 #pragma unroll
     for (int s = 16; s >= 1; s >>= 1) contrib += __shfl_xor_sync(BC_FULL, contrib, s);
-    if (lane == 0 && contrib != 0.0) p.bc[w] += contrib;
+    if (lane == 0 && !is_zero(contrib)) p.bc[w] += contrib;
     return;
   }
   // lanes belong to different requests (serving): one fixed-order sum per request
@@ -944,28 +1354,45 @@ __device__ __forceinline__ void bwd_commit(const TK &p, int w, const BwdOwner<G,
 }
 
 // Backward walk over A_d (hubs skipped): every entry is committed once, in entry order,
-// with the r rows of its successors summed in edge order.
+// with the r values of its successors summed: first the sparse hits (loaded by their edge
+// lanes), then the other hits (r rows gathered by the source lanes), each in edge order.
 template <int G, bool EXT>
 __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn, int gwarp,
                          int nwarps, int *ctr) {
   int cur = -1;
+  const int lane = lane_id();
   BwdOwner<G, EXT> o;
   walk<true>(p, p.A, p.ACD, a0, a1, E, gwarp, nwarps, ctr, [&](bool valid, int k, int, int col) {
-    uint32_t dm[G];
+    uint32_t bm[G];
     bool hit = false;
     int v = -1;
 #pragma unroll
-    for (int g = 0; g < G; g++) dm[g] = 0u;
+    for (int g = 0; g < G; g++) bm[g] = 0u;
     if (valid) {
       v = p.ci[col];
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        dm[g] = Dn[(size_t)v * G + g];
-        hit |= (dm[g] & p.AM[(size_t)k * G + g]) != 0u;
+        bm[g] = Dn[(size_t)v * G + g] & p.AM[(size_t)k * G + g];
+        hit |= bm[g] != 0u;
+      }
+    }
+    int t0 = -1, t1 = -1;
+    const bool sp = hit && two_bits<G>(bm, t0, t1) <= kSparse;
+    double r0 = 0.0, r1 = 0.0;
+    int e0 = 0, e1 = 0;
+    if (sp) {
+      const size_t i0 = (size_t)v * (32 * G) + t0;
+      r0 = p.r[i0];
+      if (EXT) e0 = p.xe[i0];
+      if (t1 >= 0) {
+        const size_t i1 = (size_t)v * (32 * G) + t1;
+        r1 = p.r[i1];
+        if (EXT) e1 = p.xe[i1];
       }
     }
     const unsigned vm = __ballot_sync(BC_FULL, valid);
-    const unsigned hits = __ballot_sync(BC_FULL, hit);
+    const unsigned sps = __ballot_sync(BC_FULL, sp);
+    const unsigned dns = __ballot_sync(BC_FULL, hit && !sp);
     if (!vm) return;
     const int k_lo = __shfl_sync(BC_FULL, k, __ffs(vm) - 1);
     const int k_hi = __shfl_sync(BC_FULL, k, 31 - __clz(vm));
@@ -977,14 +1404,27 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
         cur = kk;
         bwd_start<G, EXT>(p, kk, o);
       }
-      unsigned h = hits & lanes_k;
+      unsigned hs = sps & lanes_k, h = dns & lanes_k;
+      while (hs) {
+        const int jj = __ffs(hs) - 1;
+        hs &= hs - 1;
+#pragma unroll
+        for (int z = 0; z < 2; z++) {
+          const int t = __shfl_sync(BC_FULL, z ? t1 : t0, jj);
+          const double x = __shfl_sync(BC_FULL, z ? r1 : r0, jj);
+          const int xe = EXT ? __shfl_sync(BC_FULL, z ? e1 : e0, jj) : 0;
+#pragma unroll
+          for (int g = 0; g < G; g++)
+            if (t >= 0 && (t >> 5) == g && lane == (t & 31)) o.acc[g] += EXT ? scale2(x, o.ew[g] - xe) : x;
+        }
+      }
       if (EXT) {
         while (h) {
           const int jj = __ffs(h) - 1;
           h &= h - 1;
           uint32_t m[G];
 #pragma unroll
-          for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, dm[g], jj) & o.mw[g];
+          for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, bm[g], jj);
           bwd_hit<G, EXT>(p, __shfl_sync(BC_FULL, v, jj), m, o);
         }
       } else {
@@ -998,8 +1438,8 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
             const int vq = __shfl_sync(BC_FULL, v, jj < 0 ? 0 : jj);
 #pragma unroll
             for (int g = 0; g < G; g++) {
-              const uint32_t m = jj < 0 ? 0u : (__shfl_sync(BC_FULL, dm[g], jj < 0 ? 0 : jj) & o.mw[g]);
-              xq[q][g] = ((m >> lane_id()) & 1u) ? p.r[(size_t)vq * (32 * G) + 32 * g + lane_id()] : 0.0;
+              const uint32_t m = __shfl_sync(BC_FULL, bm[g], jj < 0 ? 0 : jj);
+              xq[q][g] = (jj >= 0 && ((m >> lane) & 1u)) ? p.r[(size_t)vq * (32 * G) + 32 * g + lane] : 0.0;
             }
           }
 #pragma unroll
@@ -1058,6 +1498,150 @@ __device__ void bwd_hub_cta(const TK &p, int k, const uint32_t *Dn, unsigned cha
   __syncthreads();
 }
 
+// One lane-mode backward pass of vertex w for sources t0 and t1 (>= 0, or -1): r of each
+// successor summed in edge order, then delta and r of (w, t); the BC contribution is added
+// to contrib (or, serving, to the sources' request buffers).
+template <int G, bool EXT>
+__device__ __forceinline__ void bwd_lane_pair(const TK &p, int w, int t0, int t1, const uint32_t *Dn,
+                                              double &contrib) {
+  double sg[2] = {1.0, 1.0}, acc[2] = {0.0, 0.0};
+  int ew[2] = {0, 0};
+  const int ts[2] = {t0, t1};
+#pragma unroll
+  for (int z = 0; z < 2; z++) {
+    if (ts[z] < 0) continue;
+    const size_t idx = (size_t)w * (32 * G) + ts[z];
+    if (EXT) {
+      const bool o = (p.ovf[(size_t)w * G + (ts[z] >> 5)] >> (ts[z] & 31)) & 1u;
+      const XS x = sig_xs(p, idx, o);
+      sg[z] = x.m;
+      ew[z] = x.e;
+    } else {
+      sg[z] = (double)p.sig[idx];
+    }
+  }
+  const int g0 = t0 >> 5, g1 = t1 >= 0 ? t1 >> 5 : g0;
+  const int e1 = p.rp[w + 1];
+  for (int e = p.rp[w]; e < e1; e += 4) {
+    int v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) v[u] = e + u < e1 ? p.ci[e + u] : -1;
+    uint32_t d0[4], d1[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      d0[u] = v[u] >= 0 ? Dn[(size_t)v[u] * G + g0] : 0u;
+      d1[u] = (v[u] >= 0 && t1 >= 0) ? (g1 == g0 ? d0[u] : Dn[(size_t)v[u] * G + g1]) : 0u;
+    }
+    double x[2][4];
+    int xe[2][4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+#pragma unroll
+      for (int z = 0; z < 2; z++) {
+        const uint32_t dm = z ? d1[u] : d0[u];
+        const bool h = ts[z] >= 0 && ((dm >> (ts[z] & 31)) & 1u);
+        const size_t idx = (size_t)v[u] * (32 * G) + ts[z];
+        x[z][u] = h ? p.r[idx] : 0.0;
+        xe[z][u] = (EXT && h) ? p.xe[idx] : 0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+      for (int z = 0; z < 2; z++) acc[z] += EXT ? scale2(x[z][u], ew[z] - xe[z][u]) : x[z][u];
+  }
+  const double om = p.omega ? (double)p.omega[w] : 0.0;
+#pragma unroll
+  for (int z = 0; z < 2; z++) {
+    if (ts[z] < 0) continue;
+    const size_t idx = (size_t)w * (32 * G) + ts[z];
+    const double delta = sg[z] * acc[z];
+    const double dl = p.wsrc[ts[z]] * delta;
+    p.r[idx] = (1.0 + delta + om) / sg[z];
+    if (EXT) p.xe[idx] = ew[z];
+    if (p.nreq == 0) {
+      contrib += dl;
+    } else if (!is_zero(dl)) {
+      p.req_bc[p.lane_req[ts[z]]][w] += dl;
+    }
+  }
+}
+
+// Lane-mode backward of entry (w, sources mw): passes over the adjacency for two sources
+// at a time, then one BC update (sources in increasing order).
+template <int G, bool EXT>
+__device__ __forceinline__ void bwd_lane_entry(const TK &p, int w, const uint32_t (&mw)[G], const uint32_t *Dn) {
+  uint32_t rem[G];
+#pragma unroll
+  for (int g = 0; g < G; g++) rem[g] = mw[g];
+  double contrib = 0.0;
+  for (;;) {
+    int t0, t1;
+    if (two_bits<G>(rem, t0, t1) == 0) break;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      if ((t0 >> 5) == g) rem[g] &= ~(1u << (t0 & 31));
+      if (t1 >= 0 && (t1 >> 5) == g) rem[g] &= ~(1u << (t1 & 31));
+    }
+    bwd_lane_pair<G, EXT>(p, w, t0, t1, Dn, contrib);
+  }
+  if (p.nreq == 0 && !is_zero(contrib)) p.bc[w] += contrib;
+}
+
+// Lane-mode backward over A_d [a0, a1): warps take 32 consecutive entries; hub entries are
+// left to the CTAs, entries with more than kLaneSrc sources or kLaneDeg edges are walked
+// warp-wide one at a time.
+template <int G, bool EXT>
+__device__ void bwd_lanes(const TK &p, int a0, int a1, const uint32_t *Dn, int gwarp, int nwarps) {
+  const int lane = lane_id();
+  for (int base = a0 + gwarp * 32; base < a1; base += nwarps * 32) {
+    const int k = base + lane;
+    const bool in = k < a1;
+    const int w = in ? p.A[k] : 0;
+    const int dg = in ? vdeg(p, w) : 0;
+    uint32_t mw[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) mw[g] = in ? p.AM[(size_t)k * G + g] : 0u;
+    int nb = 0;
+#pragma unroll
+    for (int g = 0; g < G; g++) nb += __popc(mw[g]);
+    const bool hub = dg >= kHub;
+    const bool lanep = in && !hub && dg <= kLaneDeg && nb >= 1 && nb <= kLaneSrc;
+    const bool fb = in && !hub && !lanep;
+    if (lanep) bwd_lane_entry<G, EXT>(p, w, mw, Dn);
+    unsigned fbm = __ballot_sync(BC_FULL, fb);
+    while (fbm) {
+      const int j = __ffs(fbm) - 1;
+      fbm &= fbm - 1;
+      const int kf = __shfl_sync(BC_FULL, k, j), wf = __shfl_sync(BC_FULL, w, j);
+      BwdOwner<G, EXT> o;
+      bwd_start<G, EXT>(p, kf, o);
+      const int e1 = p.rp[wf + 1];
+      for (int eb = p.rp[wf]; eb < e1; eb += 32) {
+        const int e = eb + lane;
+        const int v = e < e1 ? p.ci[e] : -1;
+        uint32_t dm[G];
+        bool hit = false;
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+          dm[g] = v >= 0 ? (Dn[(size_t)v * G + g] & o.mw[g]) : 0u;
+          hit |= dm[g] != 0u;
+        }
+        unsigned hits = __ballot_sync(BC_FULL, hit);
+        while (hits) {
+          const int jj = __ffs(hits) - 1;
+          hits &= hits - 1;
+          uint32_t m[G];
+#pragma unroll
+          for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, dm[g], jj);
+          bwd_hit<G, EXT>(p, __shfl_sync(BC_FULL, v, jj), m, o);
+        }
+      }
+      bwd_commit<G, EXT>(p, wf, o);
+    }
+  }
+}
+
 // Backward level d: hubs of A_d by whole CTAs, the rest by the walk; scatter A_d's masks
 // into the level-d buffer (read at level d-1) and clear A_{d+2}'s masks.  Three distinct
 // buffers, so one barrier per level suffices.
@@ -1071,7 +1655,10 @@ __device__ void phase_bwd_level(const TK &p, int d, int a0, int a1, int Ed, int 
     Dd[(size_t)p.A[i / G] * G + (i % G)] = p.AM[i];
   for (long long i = (long long)c0 * G + gtid; i < (long long)c1 * G; i += nthr)
     Dc[(size_t)p.A[i / G] * G + (i % G)] = 0u;
-  bwd_walk<G, EXT>(p, a0, a1, Ed, Dn, gwarp, nwarps, &p.ctl->bq[d % 3]);
+  if (lane_level(vload64(&p.Lbits[d]), a1 - a0, (long long)Ed))
+    bwd_lanes<G, EXT>(p, a0, a1, Dn, gwarp, nwarps);
+  else
+    bwd_walk<G, EXT>(p, a0, a1, Ed, Dn, gwarp, nwarps, &p.ctl->bq[d % 3]);
   // hub entries of A_d (listed at append time), one per CTA from a shared counter
   __shared__ int s_item;
   const int h0 = p.HEoff[d], h1 = p.HEoff[d + 1];
@@ -1107,7 +1694,7 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
   extern __shared__ __align__(16) unsigned char smem[];
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nthr = gridDim.x * blockDim.x;
-  const int gwarp = gtid >> 5, nwarps = nthr >> 5;
+  const int gwarp = warp_rank(), nwarps = nthr >> 5;
   GridSync *gs = &p.ctl->bar;
   phase_init_vis<G>(p, gtid, nthr);
   if (!tsync(p, gs, 0, 0)) return;
@@ -1126,8 +1713,9 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
       phase_mark<G>(p, level, a_lo, a_hi, ecnt, gwarp, nwarps);
       if (!tsync(p, gs, 1, level)) return;
     }
-    phase_pull<G, EXT>(p, level, bu, a_hi, gwarp, nwarps, smem);
+    phase_pull<G, EXT>(p, level, bu, a_lo, a_hi, gwarp, nwarps, smem);
     if (gtid == 0) {
+      p.Lbits[level] = 0ull;  // A_level's sources are counted at the next level
       p.ctl->apack[(level + 1) % 3] = 0ull;
       p.ctl->cpack[(level + 1) % 3] = 0ull;
       p.ctl->chcnt[(level + 1) % 3] = 0;
@@ -1209,7 +1797,7 @@ __global__ void __launch_bounds__(TPB<G>::value) k_fwd_mark(TK p) {
   if (c->done || c->bar.err) return;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   phase_keep<G>(p, c->level, c->a_pp, c->a_lo, c->a_hi, gtid, nthr);
-  if (!c->mode) phase_mark<G>(p, c->level, c->a_lo, c->a_hi, c->ecnt, gtid >> 5, nthr >> 5);
+  if (!c->mode) phase_mark<G>(p, c->level, c->a_lo, c->a_hi, c->ecnt, warp_rank(), nthr >> 5);
 }
 
 template <int G, bool EXT>
@@ -1218,7 +1806,7 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) k_fwd_pull(TK p) {
   const TileCtl *c = p.ctl;
   if (c->done || c->bar.err) return;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
-  phase_pull<G, EXT>(p, c->level, c->mode != 0, c->a_hi, gtid >> 5, nthr >> 5, smem);
+  phase_pull<G, EXT>(p, c->level, c->mode != 0, c->a_lo, c->a_hi, warp_rank(), nthr >> 5, smem);
 }
 
 __global__ void k_fwd_end(TK p) {
@@ -1226,6 +1814,7 @@ __global__ void k_fwd_end(TK p) {
   if (c->done || c->bar.err) return;
   int level = c->level;
   const unsigned long long pk = c->apack[level % 3];
+  p.Lbits[level] = 0ull;  // A_level's sources are counted at the next level
   c->apack[(level + 1) % 3] = 0ull;
   c->cpack[(level + 1) % 3] = 0ull;
   c->chcnt[(level + 1) % 3] = 0;
@@ -1274,7 +1863,7 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) k_bwd_level(TK p) {
     c1 = p.Aoff[d + 3];
   }
   const int a0 = p.Aoff[d], a1 = p.Aoff[d + 1];
-  phase_bwd_level<G, EXT>(p, d, a0, a1, level_edges(p, a0, a1), c0, c1, gtid, nthr, gtid >> 5,
+  phase_bwd_level<G, EXT>(p, d, a0, a1, level_edges(p, a0, a1), c0, c1, gtid, nthr, warp_rank(),
                           nthr >> 5, smem);
 }
 
@@ -1377,7 +1966,7 @@ bc_status set_attrs(int G, bool ext) {
 // ================================================================== host side
 static void ws_release(Ctx *ctx, TileWS *ws, bool main, bool ext, bool A) {
   if (main && ws->ctl) {
-    void *ptrs[] = {ws->vis, ws->F, ws->ovf, ws->cand, ws->sig, ws->r, ws->Aoff, ws->HEoff,
+    void *ptrs[] = {ws->vis, ws->F, ws->ovf, ws->cand, ws->sig, ws->r, ws->Aoff, ws->Lbits, ws->HEoff,
                     ws->C, ws->CPD, ws->Ch, ws->wsrc, ws->ctl};
     for (void *q : ptrs) cudaFree(q);
     ctx->mem.release(nullptr, ws->bytes_main);
@@ -1385,6 +1974,7 @@ static void ws_release(Ctx *ctx, TileWS *ws, bool main, bool ext, bool A) {
     ws->sig = nullptr;
     ws->r = nullptr;
     ws->Aoff = ws->HEoff = ws->C = ws->CPD = ws->Ch = nullptr;
+    ws->Lbits = nullptr;
     ws->wsrc = nullptr;
     ws->ctl = nullptr;
     ws->bytes_main = 0;
@@ -1440,8 +2030,8 @@ static bc_status ws_main(Ctx *ctx, TileWS *ws, int n, int T) {
   ws_release(ctx, ws, true, true, true);
   const int G = T / 32;
   const size_t N = (size_t)n, NG = N * G, NT = N * T;
-  const size_t bytes = NG * 4 * 5 + NT * 16 + (N / 32 + 1) * 4 + (N + 3) * 4 + N * 12 + T * 8 +
-                       sizeof(TileCtl);
+  const size_t bytes = NG * 4 * 5 + NT * 16 + (N / 32 + 1) * 4 + (N + 3) * 4 + (N + 3) * 8 + N * 12 +
+                       T * 8 + sizeof(TileCtl);
   bc_status s = ctx->mem.alloc(nullptr, bytes);
   if (s) return s;
   cudaError_t e = cudaSuccess;
@@ -1452,6 +2042,7 @@ static bc_status ws_main(Ctx *ctx, TileWS *ws, int n, int T) {
   TA(ws->sig, NT * 8);
   TA(ws->r, NT * 8);
   TA(ws->Aoff, (N + 3) * 4);
+  TA(ws->Lbits, (N + 3) * 8);
   TA(ws->HEoff, (N + 3) * 4);
   TA(ws->C, N * 4);
   TA(ws->CPD, N * 4);
@@ -1776,6 +2367,7 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
       p.AM = ws->AM;
       p.capA = ws->capA;
       p.Aoff = ws->Aoff;
+      p.Lbits = ws->Lbits;
       p.HE = ws->HE;
       p.HEoff = ws->HEoff;
       p.C = ws->C;
