@@ -101,7 +101,8 @@ struct TileWS {
   bool ext_sticky = false;  // this graph needed extended sigma before: start tiles in it
   uint32_t *vis = nullptr, *F = nullptr, *ovf = nullptr, *cand = nullptr;
   unsigned long long *sig = nullptr;
-  double *r = nullptr, *xm = nullptr;
+  float2 *r = nullptr;  // float-float r values
+  double *xm = nullptr;
   int32_t *xe = nullptr;
   int32_t *A = nullptr, *ACD = nullptr;
   uint32_t *AM = nullptr;
@@ -109,7 +110,7 @@ struct TileWS {
   unsigned long long *Lbits = nullptr;
   int32_t *HE = nullptr, *HEoff = nullptr;  // hub entries of A (positions), per-level offsets
   int32_t *C = nullptr, *CPD = nullptr, *Ch = nullptr;
-  double *wsrc = nullptr;
+  float2 *wsrc = nullptr;
   TileCtl *ctl = nullptr;
   size_t bytes_main = 0, bytes_ext = 0, bytes_A = 0;
   // per-graph lists: hubs (degree >= kHub) and the bottom-up walk list (others, deg > 0)
@@ -133,7 +134,8 @@ struct TK {
   int leaf_term;
   uint32_t *vis, *F, *ovf, *cand;
   unsigned long long *sig;
-  double *r, *xm;
+  float2 *r;  // r = (1 + delta + omega) / sigma per (vertex, source), float-float
+  double *xm;
   int32_t *xe;
   int32_t *A, *ACD;
   uint32_t *AM;
@@ -144,7 +146,7 @@ struct TK {
   int32_t *C, *CPD, *Ch;
   const int32_t *hubs, *Lbu, *PDbu;
   int nhubs, nbu, Ebu;
-  double *wsrc;
+  float2 *wsrc;  // per source: omega(s) + 1, float-float
   TileCtl *ctl;
   uint32_t unused[8];
   float alpha;
@@ -181,6 +183,27 @@ __device__ __forceinline__ int vdeg(const TK &p, int v) { return p.rp[v + 1] - p
 // Warp index for warp-level work, interleaved across CTAs (warp i of every CTA before warp
 // i + 1 of any), so that a level with few work units still spreads over all SMs.
 __device__ __forceinline__ int warp_rank() { return (int)((threadIdx.x >> 5) * gridDim.x + blockIdx.x); }
+// Row v of a [n][G] mask array in one or two vector loads (rows are 4G-byte aligned).
+template <int G>
+__device__ __forceinline__ void load_row(const uint32_t *a, long long v, uint32_t (&out)[G]) {
+  const uint32_t *r = a + (size_t)v * G;
+  if constexpr (G == 1) {
+    out[0] = r[0];
+  } else if constexpr (G == 2) {
+    const uint2 x = *(const uint2 *)r;
+    out[0] = x.x;
+    out[1] = x.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < G / 4; q++) {
+      const uint4 x = ((const uint4 *)r)[q];
+      out[4 * q] = x.x;
+      out[4 * q + 1] = x.y;
+      out[4 * q + 2] = x.z;
+      out[4 * q + 3] = x.w;
+    }
+  }
+}
 
 // Warp-aggregated append of the flagged lanes' vertices to A with its packed counter.
 __device__ __forceinline__ void append_A(const TK &p, unsigned long long *ctr, int base_off,
@@ -282,6 +305,73 @@ __device__ __forceinline__ XS xs_norm(XS a) {  // mantissa into [0.5, 1)
   a.m = __longlong_as_double((b & kMantBits) | (1022ll << 52));
   return a;
 }
+// ------------------------------------------------------------------ float-float arithmetic
+// FP64 runs at a small fraction of the FP32 rate on this GPU, so the backward sweep keeps
+// r and its sums as unevaluated pairs of floats (value hi + lo, about 48 significant
+// bits): Knuth's two-sum for additions, FMA-exact products, one Newton step for
+// reciprocals.  Sigma enters from its integer (or extended-range mantissa) bits; only the
+// per-vertex BC update is done in FP64.
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }  // k in [-126, 127]
+__device__ __forceinline__ float2 ff_norm(float s, float e) {  // |s| >= |e| (or s == 0)
+  const float hi = __fadd_rn(s, e);
+  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+__device__ __forceinline__ void ff_add(float2 &a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  a = ff_norm(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float pr = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -pr);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return ff_norm(pr, e);
+}
+// 1 / a for a > 0: y = rcp(hi), then y + y (1 - a y) (1 - hi y is exact: hi y ~ 1)
+__device__ __forceinline__ float2 ff_rcp(float2 a) {
+  const float y = __frcp_rn(a.x);
+  const float pr = __fmul_rn(a.x, y);
+  float e = __fmaf_rn(a.x, y, -pr);
+  e = __fmaf_rn(a.y, y, e);
+  const float t = __fsub_rn(__fsub_rn(1.0f, pr), e);
+  return ff_norm(y, __fmul_rn(y, t));
+}
+// a nonzero integer: its top 24 bits and the next 24 (the rest is truncated, < 2^-47)
+__device__ __forceinline__ float2 ff_u64(unsigned long long s) {
+  const int lz = __clzll((long long)s);
+  const unsigned long long t = s << lz;
+  const int e = 63 - lz;
+  const float hi = __uint2float_rn((unsigned)(t >> 40)) * pow2f(e - 23);
+  const float lo = __uint2float_rn((unsigned)(t >> 16) & 0xffffffu) * pow2f(e - 47);
+  return ff_norm(hi, lo);
+}
+// an extended-range mantissa m in [0.5, 1)
+__device__ __forceinline__ float2 ff_mant(double m) {
+  const unsigned long long mant =
+      ((unsigned long long)__double_as_longlong(m) & (unsigned long long)kMantBits) | (1ull << 52);
+  const float2 a = ff_u64(mant);  // m = mant * 2^-53
+  return make_float2(a.x * pow2f(-53), a.y * pow2f(-53));
+}
+// a * 2^k (k <= 0); parts below the normal float range become 0 (they join sums of terms
+// of the same scale near 1, far below the rounding)
+__device__ __forceinline__ float scale2f(float m, int k) {
+  const int b = __float_as_int(m);
+  const int ne = ((b >> 23) & 0xff) + k;
+  if ((b & 0x7fffffff) == 0 || ne <= 0) return 0.0f;
+  return __int_as_float((b & (int)0x807fffff) | (ne << 23));
+}
+__device__ __forceinline__ float2 ff_scale(float2 a, int k) { return make_float2(scale2f(a.x, k), scale2f(a.y, k)); }
+__device__ __forceinline__ double ff_to(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ bool ff_zero(float2 a) { return a.x == 0.0f && a.y == 0.0f; }
+__device__ __forceinline__ float2 ff_shfl(float2 a, int src) {
+  return make_float2(__shfl_sync(BC_FULL, a.x, src), __shfl_sync(BC_FULL, a.y, src));
+}
+__device__ __forceinline__ float2 ff_shfl_xor(float2 a, int m) {
+  return make_float2(__shfl_xor_sync(BC_FULL, a.x, m), __shfl_xor_sync(BC_FULL, a.y, m));
+}
+
 __device__ __forceinline__ XS sig_xs(const TK &p, size_t idx, bool o) {
   if (o) {
     XS x;
@@ -477,11 +567,9 @@ __device__ __forceinline__ bool pull_commit(const TK &p, int w, int level, const
 template <int G>
 __device__ __forceinline__ bool load_vis(const TK &p, int w, uint32_t (&visw)[G]) {
   bool full = true;
+  load_row<G>(p.vis, w, visw);
 #pragma unroll
-  for (int g = 0; g < G; g++) {
-    visw[g] = p.vis[(size_t)w * G + g];
-    full &= visw[g] == 0xffffffffu;
-  }
+  for (int g = 0; g < G; g++) full &= visw[g] == 0xffffffffu;
   return full;
 }
 
@@ -557,9 +645,10 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
     bool hit = false;
     if (valid && !full) {
       pj = p.ci[col];
+      load_row<G>(Fp, pj, bm);
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        bm[g] = Fp[(size_t)pj * G + g] & ~vw[g];
+        bm[g] &= ~vw[g];
         hit |= bm[g] != 0u;
       }
     }
@@ -707,11 +796,14 @@ __device__ bool pull_hub_cta(const TK &p, int w, int level, bool leaf,
     const int pj = jdx < hi ? p.ci[jdx] : -1;
     uint32_t fm[G];
     bool hit = false;
+    if (pj >= 0) {
+      load_row<G>(Fp, pj, fm);
+    } else {
 #pragma unroll
-    for (int g = 0; g < G; g++) {
-      fm[g] = pj >= 0 ? Fp[(size_t)pj * G + g] : 0u;
-      hit |= (fm[g] & ~visw[g]) != 0u;
+      for (int g = 0; g < G; g++) fm[g] = 0u;
     }
+#pragma unroll
+    for (int g = 0; g < G; g++) hit |= (fm[g] & ~visw[g]) != 0u;
     unsigned hits = __ballot_sync(BC_FULL, hit);
     while (hits) {
       const int jj = __ffs(hits) - 1;
@@ -823,9 +915,16 @@ __device__ __forceinline__ void lane_pull(const TK &p, const uint32_t *Fp, int w
     for (int u = 0; u < 4; u++) pj[u] = e + u < e1 ? p.ci[e + u] : -1;
     uint32_t fm[4][G];
 #pragma unroll
-    for (int u = 0; u < 4; u++)
+    for (int u = 0; u < 4; u++) {
+      if (pj[u] >= 0) {
+        load_row<G>(Fp, pj[u], fm[u]);
 #pragma unroll
-      for (int g = 0; g < G; g++) fm[u][g] = pj[u] >= 0 ? (Fp[(size_t)pj[u] * G + g] & ~vw[g]) : 0u;
+        for (int g = 0; g < G; g++) fm[u][g] &= ~vw[g];
+      } else {
+#pragma unroll
+        for (int g = 0; g < G; g++) fm[u][g] = 0u;
+      }
+    }
 #pragma unroll
     for (int u = 0; u < 4; u++) {
 #pragma unroll
@@ -941,9 +1040,15 @@ __device__ bool warp_pull_one(const TK &p, int level, int w, const uint32_t (&vi
     const int pj = e < e1 ? p.ci[e] : -1;
     uint32_t fm[G];
     bool hit = false;
+    if (pj >= 0) {
+      load_row<G>(Fp, pj, fm);
+    } else {
+#pragma unroll
+      for (int g = 0; g < G; g++) fm[g] = 0u;
+    }
 #pragma unroll
     for (int g = 0; g < G; g++) {
-      fm[g] = pj >= 0 ? (Fp[(size_t)pj * G + g] & ~visc[g]) : 0u;
+      fm[g] &= ~visc[g];
       hit |= fm[g] != 0u;
     }
     unsigned hits = __ballot_sync(BC_FULL, hit);
@@ -1145,8 +1250,11 @@ __device__ void phase_mark(const TK &p, int level, int a0, int a1, int E1, int g
     if (my < ee) {
       w = p.ci[col];
       bool hit = false;
+      uint32_t fv[G], vv[G];
+      load_row<G>(Fp, v, fv);
+      load_row<G>(p.vis, w, vv);
 #pragma unroll
-      for (int g = 0; g < G; g++) hit |= (Fp[(size_t)v * G + g] & ~p.vis[(size_t)w * G + g]) != 0u;
+      for (int g = 0; g < G; g++) hit |= (fv[g] & ~vv[g]) != 0u;
       if (hit) {
         const uint32_t bit = 1u << (w & 31);
         isc = !(atomicOr(p.cand + (w >> 5), bit) & bit);
@@ -1249,48 +1357,48 @@ __device__ void phase_bwd_deep(const TK &p, int a0, int a1, int gtid, int nthr) 
     const uint32_t m = p.AM[(size_t)k * G + g];
     if (!((m >> ln) & 1u)) continue;
     const int w = p.A[k];
-    const double om = p.omega ? (double)p.omega[w] : 0.0;
+    const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
     const size_t idx = (size_t)w * (32 * G) + t;
-    double sg;
+    float2 sg;
     if (EXT) {
       const bool o = (p.ovf[(size_t)w * G + g] >> ln) & 1u;
       const XS x = sig_xs(p, idx, o);
-      sg = x.m;
+      sg = ff_mant(x.m);
       if (!o) p.xe[idx] = x.e;
     } else {
-      sg = (double)p.sig[idx];
+      sg = ff_u64(p.sig[idx]);
     }
-    p.r[idx] = (1.0 + om) / sg;
+    p.r[idx] = ff_mul(om1, ff_rcp(sg));
   }
 }
 
 template <int G, bool EXT>
 struct BwdOwner {
   uint32_t mw[G];
-  double sg[G];
+  float2 sg[G];  // sigma (extended: its mantissa), float-float
   int ew[EXT ? G : 1];
-  double acc[G];
+  float2 acc[G];  // sum of the successors' r
 };
 
 template <int G, bool EXT>
 __device__ __forceinline__ void bwd_start(const TK &p, int k, BwdOwner<G, EXT> &o) {
   const int lane = lane_id();
   const int w = p.A[k];
+  load_row<G>(p.AM, k, o.mw);
 #pragma unroll
   for (int g = 0; g < G; g++) {
-    o.mw[g] = p.AM[(size_t)k * G + g];
-    o.sg[g] = 1.0;
-    o.acc[g] = 0.0;
+    o.sg[g] = make_float2(1.0f, 0.0f);
+    o.acc[g] = make_float2(0.0f, 0.0f);
     if (EXT) o.ew[g] = 0;
     if ((o.mw[g] >> lane) & 1u) {
       const size_t idx = (size_t)w * (32 * G) + 32 * g + lane;
       if (EXT) {
         const bool ov = (p.ovf[(size_t)w * G + g] >> lane) & 1u;
         const XS x = sig_xs(p, idx, ov);
-        o.sg[g] = x.m;
+        o.sg[g] = ff_mant(x.m);
         o.ew[g] = x.e;
       } else {
-        o.sg[g] = (double)p.sig[idx];
+        o.sg[g] = ff_u64(p.sig[idx]);
       }
     }
   }
@@ -1303,9 +1411,9 @@ __device__ __forceinline__ void bwd_hit(const TK &p, int v, const uint32_t (&m)[
   for (int g = 0; g < G; g++) {
     if ((m[g] >> lane) & 1u) {
       const size_t idx = (size_t)v * (32 * G) + 32 * g + lane;
-      double x = p.r[idx];
-      if (EXT) x = scale2(x, o.ew[g] - p.xe[idx]);
-      o.acc[g] += x;
+      float2 x = p.r[idx];
+      if (EXT) x = ff_scale(x, o.ew[g] - p.xe[idx]);
+      ff_add(o.acc[g], x);
     }
   }
 }
@@ -1313,18 +1421,20 @@ __device__ __forceinline__ void bwd_hit(const TK &p, int v, const uint32_t (&m)[
 template <int G, bool EXT>
 __device__ __forceinline__ void bwd_commit(const TK &p, int w, const BwdOwner<G, EXT> &o) {
   const int lane = lane_id();
-  const double om = p.omega ? (double)p.omega[w] : 0.0;
-  double contrib = 0.0;
-  double dl[G];
+  const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
+  float2 contrib = make_float2(0.0f, 0.0f);
+  float2 dl[G];
 #pragma unroll
   for (int g = 0; g < G; g++) {
-    dl[g] = 0.0;
+    dl[g] = make_float2(0.0f, 0.0f);
     if ((o.mw[g] >> lane) & 1u) {
       const size_t idx = (size_t)w * (32 * G) + 32 * g + lane;
-      const double delta = o.sg[g] * o.acc[g];
-      dl[g] = p.wsrc[32 * g + lane] * delta;
-      contrib += dl[g];
-      p.r[idx] = (1.0 + delta + om) / o.sg[g];
+      // delta = sigma * sum r(succ);  r = (1 + delta + omega) / sigma = (1 + omega) / sigma + sum
+      dl[g] = ff_mul(p.wsrc[32 * g + lane], ff_mul(o.sg[g], o.acc[g]));
+      ff_add(contrib, dl[g]);
+      float2 r = ff_mul(om1, ff_rcp(o.sg[g]));
+      ff_add(r, o.acc[g]);
+      p.r[idx] = r;
       if (EXT) p.xe[idx] = o.ew[g];
     }
   }
@@ -1332,24 +1442,24 @@ __device__ __forceinline__ void bwd_commit(const TK &p, int w, const BwdOwner<G,
     unsigned act = 0u;
 #pragma unroll
     for (int g = 0; g < G; g++) act |= o.mw[g];
-    if (__popc(act) == 1) {  // one lane holds the whole sum (the reduction would add zeros)
-      if (lane == __ffs(act) - 1 && !is_zero(contrib)) p.bc[w] += contrib;
+    if (__popc(act) == 1) {  // one lane holds the whole sum
+      if (lane == __ffs(act) - 1 && !ff_zero(contrib)) p.bc[w] += ff_to(contrib);
       return;
     }
 #pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) contrib += __shfl_xor_sync(BC_FULL, contrib, s);
-    if (lane == 0 && !is_zero(contrib)) p.bc[w] += contrib;
+    for (int m = 16; m >= 1; m >>= 1) ff_add(contrib, ff_shfl_xor(contrib, m));
+    if (lane == 0 && !ff_zero(contrib)) p.bc[w] += ff_to(contrib);
     return;
   }
   // lanes belong to different requests (serving): one fixed-order sum per request
   for (int q = 0; q < p.nreq; q++) {
-    double c = 0.0;
+    float2 c = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int g = 0; g < G; g++)
-      if (((o.mw[g] >> lane) & 1u) && p.lane_req[32 * g + lane] == q) c += dl[g];
+      if (((o.mw[g] >> lane) & 1u) && p.lane_req[32 * g + lane] == q) ff_add(c, dl[g]);
 #pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) c += __shfl_xor_sync(BC_FULL, c, s);
-    if (lane == 0 && c != 0.0) p.req_bc[q][w] += c;
+    for (int m = 16; m >= 1; m >>= 1) ff_add(c, ff_shfl_xor(c, m));
+    if (lane == 0 && !ff_zero(c)) p.req_bc[q][w] += ff_to(c);
   }
 }
 
@@ -1370,15 +1480,18 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
     for (int g = 0; g < G; g++) bm[g] = 0u;
     if (valid) {
       v = p.ci[col];
+      uint32_t am[G];
+      load_row<G>(Dn, v, bm);
+      load_row<G>(p.AM, k, am);
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        bm[g] = Dn[(size_t)v * G + g] & p.AM[(size_t)k * G + g];
+        bm[g] &= am[g];
         hit |= bm[g] != 0u;
       }
     }
     int t0 = -1, t1 = -1;
     const bool sp = hit && two_bits<G>(bm, t0, t1) <= kSparse;
-    double r0 = 0.0, r1 = 0.0;
+    float2 r0 = make_float2(0.0f, 0.0f), r1 = make_float2(0.0f, 0.0f);
     int e0 = 0, e1 = 0;
     if (sp) {
       const size_t i0 = (size_t)v * (32 * G) + t0;
@@ -1411,11 +1524,11 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
 #pragma unroll
         for (int z = 0; z < 2; z++) {
           const int t = __shfl_sync(BC_FULL, z ? t1 : t0, jj);
-          const double x = __shfl_sync(BC_FULL, z ? r1 : r0, jj);
+          const float2 x = ff_shfl(z ? r1 : r0, jj);
           const int xe = EXT ? __shfl_sync(BC_FULL, z ? e1 : e0, jj) : 0;
 #pragma unroll
           for (int g = 0; g < G; g++)
-            if (t >= 0 && (t >> 5) == g && lane == (t & 31)) o.acc[g] += EXT ? scale2(x, o.ew[g] - xe) : x;
+            if (t >= 0 && (t >> 5) == g && lane == (t & 31)) ff_add(o.acc[g], EXT ? ff_scale(x, o.ew[g] - xe) : x);
         }
       }
       if (EXT) {
@@ -1430,7 +1543,8 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
       } else {
         // up to HB<G>::value successors at a time: their r-row loads are in flight together
         while (h) {
-          double xq[HB<G>::value][G];
+          float2 xq[HB<G>::value][G];
+          uint32_t mq[HB<G>::value][G];
 #pragma unroll
           for (int q = 0; q < HB<G>::value; q++) {
             const int jj = h ? __ffs(h) - 1 : -1;
@@ -1439,13 +1553,16 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
 #pragma unroll
             for (int g = 0; g < G; g++) {
               const uint32_t m = __shfl_sync(BC_FULL, bm[g], jj < 0 ? 0 : jj);
-              xq[q][g] = (jj >= 0 && ((m >> lane) & 1u)) ? p.r[(size_t)vq * (32 * G) + 32 * g + lane] : 0.0;
+              mq[q][g] = jj < 0 ? 0u : m;
+              xq[q][g] = ((mq[q][g] >> lane) & 1u) ? p.r[(size_t)vq * (32 * G) + 32 * g + lane]
+                                                   : make_float2(0.0f, 0.0f);
             }
           }
 #pragma unroll
           for (int q = 0; q < HB<G>::value; q++)
 #pragma unroll
-            for (int g = 0; g < G; g++) o.acc[g] += xq[q][g];
+            for (int g = 0; g < G; g++)
+              if (mq[q][g]) ff_add(o.acc[g], xq[q][g]);
         }
       }
     }
@@ -1467,11 +1584,14 @@ __device__ void bwd_hub_cta(const TK &p, int k, const uint32_t *Dn, unsigned cha
     const int v = jdx < hi ? p.ci[jdx] : -1;
     uint32_t dm[G];
     bool hit = false;
+    if (v >= 0) {
+      load_row<G>(Dn, v, dm);
+    } else {
 #pragma unroll
-    for (int g = 0; g < G; g++) {
-      dm[g] = v >= 0 ? Dn[(size_t)v * G + g] : 0u;
-      hit |= (dm[g] & o.mw[g]) != 0u;
+      for (int g = 0; g < G; g++) dm[g] = 0u;
     }
+#pragma unroll
+    for (int g = 0; g < G; g++) hit |= (dm[g] & o.mw[g]) != 0u;
     unsigned hits = __ballot_sync(BC_FULL, hit);
     while (hits) {
       const int jj = __ffs(hits) - 1;
@@ -1482,16 +1602,16 @@ __device__ void bwd_hub_cta(const TK &p, int k, const uint32_t *Dn, unsigned cha
       bwd_hit<G, EXT>(p, __shfl_sync(BC_FULL, v, jj), m, o);
     }
   }
-  double *sa = (double *)smem;
+  float2 *sa = (float2 *)smem;
 #pragma unroll 1
   for (int g = 0; g < G; g++) {
     __syncthreads();
     sa[wid * 32 + lane] = o.acc[g];
     __syncthreads();
     if (wid == 0) {
-      double s = 0.0;
-      for (int q = 0; q < nw; q++) s += sa[q * 32 + lane];
-      o.acc[g] = s;
+      float2 sum = make_float2(0.0f, 0.0f);
+      for (int q = 0; q < nw; q++) ff_add(sum, sa[q * 32 + lane]);
+      o.acc[g] = sum;
     }
   }
   if (wid == 0) bwd_commit<G, EXT>(p, w, o);
@@ -1503,8 +1623,9 @@ __device__ void bwd_hub_cta(const TK &p, int k, const uint32_t *Dn, unsigned cha
 // to contrib (or, serving, to the sources' request buffers).
 template <int G, bool EXT>
 __device__ __forceinline__ void bwd_lane_pair(const TK &p, int w, int t0, int t1, const uint32_t *Dn,
-                                              double &contrib) {
-  double sg[2] = {1.0, 1.0}, acc[2] = {0.0, 0.0};
+                                              float2 &contrib) {
+  float2 sg[2] = {make_float2(1.0f, 0.0f), make_float2(1.0f, 0.0f)};
+  float2 acc[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
   int ew[2] = {0, 0};
   const int ts[2] = {t0, t1};
 #pragma unroll
@@ -1514,10 +1635,10 @@ __device__ __forceinline__ void bwd_lane_pair(const TK &p, int w, int t0, int t1
     if (EXT) {
       const bool o = (p.ovf[(size_t)w * G + (ts[z] >> 5)] >> (ts[z] & 31)) & 1u;
       const XS x = sig_xs(p, idx, o);
-      sg[z] = x.m;
+      sg[z] = ff_mant(x.m);
       ew[z] = x.e;
     } else {
-      sg[z] = (double)p.sig[idx];
+      sg[z] = ff_u64(p.sig[idx]);
     }
   }
   const int g0 = t0 >> 5, g1 = t1 >= 0 ? t1 >> 5 : g0;
@@ -1532,7 +1653,7 @@ __device__ __forceinline__ void bwd_lane_pair(const TK &p, int w, int t0, int t1
       d0[u] = v[u] >= 0 ? Dn[(size_t)v[u] * G + g0] : 0u;
       d1[u] = (v[u] >= 0 && t1 >= 0) ? (g1 == g0 ? d0[u] : Dn[(size_t)v[u] * G + g1]) : 0u;
     }
-    double x[2][4];
+    float2 x[2][4];
     int xe[2][4];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
@@ -1541,28 +1662,29 @@ __device__ __forceinline__ void bwd_lane_pair(const TK &p, int w, int t0, int t1
         const uint32_t dm = z ? d1[u] : d0[u];
         const bool h = ts[z] >= 0 && ((dm >> (ts[z] & 31)) & 1u);
         const size_t idx = (size_t)v[u] * (32 * G) + ts[z];
-        x[z][u] = h ? p.r[idx] : 0.0;
+        x[z][u] = h ? p.r[idx] : make_float2(0.0f, 0.0f);
         xe[z][u] = (EXT && h) ? p.xe[idx] : 0;
       }
     }
 #pragma unroll
     for (int u = 0; u < 4; u++)
 #pragma unroll
-      for (int z = 0; z < 2; z++) acc[z] += EXT ? scale2(x[z][u], ew[z] - xe[z][u]) : x[z][u];
+      for (int z = 0; z < 2; z++) ff_add(acc[z], EXT ? ff_scale(x[z][u], ew[z] - xe[z][u]) : x[z][u]);
   }
-  const double om = p.omega ? (double)p.omega[w] : 0.0;
+  const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
 #pragma unroll
   for (int z = 0; z < 2; z++) {
     if (ts[z] < 0) continue;
     const size_t idx = (size_t)w * (32 * G) + ts[z];
-    const double delta = sg[z] * acc[z];
-    const double dl = p.wsrc[ts[z]] * delta;
-    p.r[idx] = (1.0 + delta + om) / sg[z];
+    const float2 dl = ff_mul(p.wsrc[ts[z]], ff_mul(sg[z], acc[z]));
+    float2 r = ff_mul(om1, ff_rcp(sg[z]));
+    ff_add(r, acc[z]);
+    p.r[idx] = r;
     if (EXT) p.xe[idx] = ew[z];
     if (p.nreq == 0) {
-      contrib += dl;
-    } else if (!is_zero(dl)) {
-      p.req_bc[p.lane_req[ts[z]]][w] += dl;
+      ff_add(contrib, dl);
+    } else if (!ff_zero(dl)) {
+      p.req_bc[p.lane_req[ts[z]]][w] += ff_to(dl);
     }
   }
 }
@@ -1574,7 +1696,7 @@ __device__ __forceinline__ void bwd_lane_entry(const TK &p, int w, const uint32_
   uint32_t rem[G];
 #pragma unroll
   for (int g = 0; g < G; g++) rem[g] = mw[g];
-  double contrib = 0.0;
+  float2 contrib = make_float2(0.0f, 0.0f);
   for (;;) {
     int t0, t1;
     if (two_bits<G>(rem, t0, t1) == 0) break;
@@ -1585,7 +1707,7 @@ __device__ __forceinline__ void bwd_lane_entry(const TK &p, int w, const uint32_
     }
     bwd_lane_pair<G, EXT>(p, w, t0, t1, Dn, contrib);
   }
-  if (p.nreq == 0 && !is_zero(contrib)) p.bc[w] += contrib;
+  if (p.nreq == 0 && !ff_zero(contrib)) p.bc[w] += ff_to(contrib);
 }
 
 // Lane-mode backward over A_d [a0, a1): warps take 32 consecutive entries; hub entries are
@@ -1600,8 +1722,12 @@ __device__ void bwd_lanes(const TK &p, int a0, int a1, const uint32_t *Dn, int g
     const int w = in ? p.A[k] : 0;
     const int dg = in ? vdeg(p, w) : 0;
     uint32_t mw[G];
+    if (in) {
+      load_row<G>(p.AM, k, mw);
+    } else {
 #pragma unroll
-    for (int g = 0; g < G; g++) mw[g] = in ? p.AM[(size_t)k * G + g] : 0u;
+      for (int g = 0; g < G; g++) mw[g] = 0u;
+    }
     int nb = 0;
 #pragma unroll
     for (int g = 0; g < G; g++) nb += __popc(mw[g]);
@@ -1622,9 +1748,15 @@ __device__ void bwd_lanes(const TK &p, int a0, int a1, const uint32_t *Dn, int g
         const int v = e < e1 ? p.ci[e] : -1;
         uint32_t dm[G];
         bool hit = false;
+        if (v >= 0) {
+          load_row<G>(Dn, v, dm);
+        } else {
+#pragma unroll
+          for (int g = 0; g < G; g++) dm[g] = 0u;
+        }
 #pragma unroll
         for (int g = 0; g < G; g++) {
-          dm[g] = v >= 0 ? (Dn[(size_t)v * G + g] & o.mw[g]) : 0u;
+          dm[g] &= o.mw[g];
           hit |= dm[g] != 0u;
         }
         unsigned hits = __ballot_sync(BC_FULL, hit);
@@ -1923,9 +2055,10 @@ __global__ void k_lists_fill(int32_t n, const int32_t *rp, const int32_t *flag, 
     }
 }
 
-__global__ void k_wsrc(const int32_t *src, int nsrc, const int32_t *omega, double *wsrc, int T) {
+__global__ void k_wsrc(const int32_t *src, int nsrc, const int32_t *omega, float2 *wsrc, int T) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < T) wsrc[t] = t < nsrc ? (omega ? (double)omega[src[t]] + 1.0 : 1.0) : 0.0;
+  if (t < T)
+    wsrc[t] = t < nsrc ? ff_u64(1ull + (omega ? (unsigned long long)omega[src[t]] : 0ull)) : make_float2(0.0f, 0.0f);
 }
 
 // ------------------------------------------------------------------ host dispatch helpers
