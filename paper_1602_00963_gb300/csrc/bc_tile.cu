@@ -64,7 +64,7 @@ struct TPB {  // threads per CTA: wide tiles keep more state per lane
 // issue G loads per hit)
 template <int G>
 struct HB {
-  static constexpr int value = G >= 8 ? 1 : (G >= 2 ? 2 : 4);
+  static constexpr int value = G >= 8 ? 2 : (G >= 2 ? 4 : 8);
 };
 
 struct TileCtl {
@@ -75,8 +75,8 @@ struct TileCtl {
   int hecnt;                    // hub entries listed in HE
   int hubq[3];                  // forward hub work counter (slot l % 3)
   int bhubq[3];                 // backward hub work counter (slot d % 3)
-  int wq[3];                    // forward pull walk chunk counter (slot l % 3)
-  int bq[3];                    // backward walk chunk counter (slot d % 3)
+  unsigned long long wq[3];     // forward pull walk: edges claimed (slot l % 3)
+  unsigned long long bq[3];     // backward walk: edges claimed (slot d % 3)
   int ovf_any;                  // some sigma of this tile passed 2^64
   unsigned ovf_lanes[8];        // lanes (sources) with an overflowed sigma
   // launched / graph mode registers
@@ -446,29 +446,44 @@ __device__ __forceinline__ void walk_range(const TK &p, const int32_t *L, const 
   }
 }
 
-// The walk over all E edges in chunks: each warp starts with chunk number gwarp, further
-// chunks are claimed from a shared counter (slow chunks, with many hits, do not hold up a
-// whole static slice).  Chunks hold E / (4 * warps) edges, between 32 and kChunk, so that
-// short levels still spread over all warps.  The next chunk is claimed before the current
-// one is walked, hiding the atomic's latency.
+// The walk over all E edges: each warp first takes a static chunk (number gwarp), then
+// claims further ranges from a shared edge counter, guided: a claim takes about half the
+// remaining edges' per-warp share, between 32 and kChunk, so that ranges shrink towards
+// the end of the level and warps finish together.  The next range is claimed before the
+// current one is walked, hiding the atomic's latency.
 constexpr int kChunk = 1024;
 
 template <bool SKIP_HUBS, typename F>
 __device__ __forceinline__ void walk(const TK &p, const int32_t *L, const int32_t *PD, int i_lo,
-                                     int i_hi, int E, int gwarp, int nwarps, int *ctr, F &&f) {
+                                     int i_hi, int E, int gwarp, int nwarps, unsigned long long *ctr, F &&f) {
   if (E <= 0 || i_hi <= i_lo) return;
   long long ch = ((long long)E / (4ll * nwarps) + 31) & ~31ll;
   ch = ch < 32 ? 32 : (ch > kChunk ? kChunk : ch);
-  const long long nch = ((long long)E + ch - 1) / ch;
-  long long c = gwarp;
-  while (c < nch) {
-    int cn = 0;
-    if (nch > nwarps && lane_id() == 0) cn = atomicAdd(ctr, 1);
-    const long long next = (nch > nwarps) ? (long long)nwarps + __shfl_sync(BC_FULL, cn, 0) : nch;
-    const long long eb = c * ch;
-    const int ee = (int)min(eb + ch, (long long)E);
-    walk_range<SKIP_HUBS>(p, L, PD, i_lo, i_hi, E, (int)eb, ee, f);
-    c = next;
+  const long long base0 = ch * nwarps;  // edges of the static first chunks
+  long long eb = (long long)gwarp * ch;
+  long long ee = min(eb + ch, (long long)E);
+  while (eb < E) {
+    long long nb = E, ne = E;
+    if (base0 < E) {
+      long long off = 0, sz = 0;
+      if (lane_id() == 0) {
+        const long long left = (long long)E - base0 - (long long)*(volatile unsigned long long *)ctr;
+        if (left > 0) {
+          sz = ((left / (2ll * nwarps)) + 31) & ~31ll;
+          sz = sz < 32 ? 32 : (sz > kChunk ? kChunk : sz);
+          off = (long long)atomicAdd(ctr, (unsigned long long)sz);
+        } else {
+          off = (long long)E;  // nothing left
+        }
+      }
+      off = __shfl_sync(BC_FULL, off, 0);
+      sz = __shfl_sync(BC_FULL, sz, 0);
+      nb = min(base0 + off, (long long)E);
+      ne = min(nb + sz, (long long)E);
+    }
+    walk_range<SKIP_HUBS>(p, L, PD, i_lo, i_hi, E, (int)eb, (int)ee, f);
+    eb = nb;
+    ee = ne;
   }
 }
 
@@ -615,6 +630,125 @@ __device__ __forceinline__ void pull_sparse_add(PullAcc<G, EXT> &a, int t, unsig
   }
 }
 
+// One forward edge per lane: frontier neighbour pj and the sources bm it brings to the
+// owner; hits of at most kSparse sources carry their own sigma values.
+template <int G, bool EXT>
+struct FwdHit {
+  int pj;
+  uint32_t bm[G];
+  bool hit, sp;
+  int t0, t1;
+  unsigned long long s0, s1;
+  bool o0, o1;
+  XS x0, x1;
+};
+
+template <int G, bool EXT>
+__device__ __forceinline__ void fwd_hit_load(const TK &p, FwdHit<G, EXT> &h) {
+  h.t0 = h.t1 = -1;
+  h.sp = h.hit && two_bits<G>(h.bm, h.t0, h.t1) <= kSparse;
+  h.s0 = h.s1 = 0ull;
+  h.o0 = h.o1 = false;
+  h.x0.m = h.x1.m = 0.0;
+  h.x0.e = h.x1.e = 0;
+  if (!h.sp) return;
+  const size_t i0 = (size_t)h.pj * (32 * G) + h.t0;
+  h.s0 = p.sig[i0];
+  h.o0 = (p.ovf[(size_t)h.pj * G + (h.t0 >> 5)] >> (h.t0 & 31)) & 1u;
+  const size_t i1 = (size_t)h.pj * (32 * G) + (h.t1 >= 0 ? h.t1 : h.t0);
+  if (h.t1 >= 0) {
+    h.s1 = p.sig[i1];
+    h.o1 = (p.ovf[(size_t)h.pj * G + (h.t1 >> 5)] >> (h.t1 & 31)) & 1u;
+  }
+  if (EXT) {
+    if (h.o0) {
+      h.x0.m = p.xm[i0];
+      h.x0.e = p.xe[i0];
+    } else {
+      h.x0 = xs_u64(h.s0);
+    }
+    if (h.t1 >= 0) {
+      if (h.o1) {
+        h.x1.m = p.xm[i1];
+        h.x1.e = p.xe[i1];
+      } else {
+        h.x1 = xs_u64(h.s1);
+      }
+    }
+  }
+}
+
+// Add the hits of lanes hs (sparse) and hd (the others), all of one owner, to a: sparse
+// terms by shuffles, the others by sigma-row gathers (HB<G> rows in flight together).
+template <int G, bool EXT>
+__device__ __forceinline__ void fwd_hits_add(const TK &p, const FwdHit<G, EXT> &h, unsigned hs, unsigned hd,
+                                             PullAcc<G, EXT> &a) {
+  const int lane = lane_id();
+  while (hs) {
+    const int jj = __ffs(hs) - 1;
+    hs &= hs - 1;
+    const int u0 = __shfl_sync(BC_FULL, h.t0, jj), u1 = __shfl_sync(BC_FULL, h.t1, jj);
+    XS y0, y1;
+    y0.m = y1.m = 0.0;
+    y0.e = y1.e = 0;
+    if (EXT) {
+      y0.m = __shfl_sync(BC_FULL, h.x0.m, jj);
+      y0.e = __shfl_sync(BC_FULL, h.x0.e, jj);
+    }
+    pull_sparse_add<G, EXT>(a, u0, __shfl_sync(BC_FULL, h.s0, jj), __shfl_sync(BC_FULL, h.o0, jj), y0);
+    if (u1 >= 0) {
+      if (EXT) {
+        y1.m = __shfl_sync(BC_FULL, h.x1.m, jj);
+        y1.e = __shfl_sync(BC_FULL, h.x1.e, jj);
+      }
+      pull_sparse_add<G, EXT>(a, u1, __shfl_sync(BC_FULL, h.s1, jj), __shfl_sync(BC_FULL, h.o1, jj), y1);
+    }
+  }
+  if (EXT) {
+    while (hd) {
+      const int jj = __ffs(hd) - 1;
+      hd &= hd - 1;
+      uint32_t m[G];
+#pragma unroll
+      for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, h.bm[g], jj);
+      pull_hit<G, EXT>(p, __shfl_sync(BC_FULL, h.pj, jj), m, a);
+    }
+    return;
+  }
+  while (hd) {
+    unsigned long long sv[HB<G>::value][G];
+    uint32_t mq[HB<G>::value][G];
+    uint32_t povf[HB<G>::value];
+#pragma unroll
+    for (int q = 0; q < HB<G>::value; q++) {
+      const int jq = hd ? __ffs(hd) - 1 : -1;
+      if (hd) hd &= hd - 1;
+      const int pn = __shfl_sync(BC_FULL, h.pj, jq < 0 ? 0 : jq);
+      povf[q] = 0u;
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        const uint32_t m = __shfl_sync(BC_FULL, h.bm[g], jq < 0 ? 0 : jq);
+        mq[q][g] = jq < 0 ? 0u : m;
+        sv[q][g] = 0ull;
+        if ((mq[q][g] >> lane) & 1u) {
+          sv[q][g] = p.sig[(size_t)pn * (32 * G) + 32 * g + lane];
+          if ((p.ovf[(size_t)pn * G + g] >> lane) & 1u) povf[q] |= 1u << g;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < HB<G>::value; q++) {
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        a.newm[g] |= mq[q][g];
+        const unsigned long long old = a.s[g];
+        a.s[g] = old + sv[q][g];
+        if (a.s[g] < old || ((povf[q] >> g) & 1u)) a.o |= 1u << g;
+      }
+    }
+  }
+}
+
 // Forward pull over the walk of list L: lanes test the edges' frontier masks against their
 // owner's unvisited mask; then, owner by owner, the sparse hits (loaded by their lanes)
 // and the other hits (sigma rows gathered by the source lanes) are summed, each set in
@@ -624,7 +758,6 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
                           int E, int gwarp, int nwarps, AppendBuf &ab, unsigned long long *ap,
                           int a_base, bool leaf, unsigned long long (&nsacc)[G]) {
   const uint32_t *Fp = Fbuf<G>(p, level - 1);
-  const int lane = lane_id();
   int cur = -1;
   uint32_t visc[G];
   PullAcc<G, EXT> a;
@@ -633,68 +766,36 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
   for (int g = 0; g < G; g++) visc[g] = 0u;
   walk<false>(p, L, PD, 0, n_list, E, gwarp, nwarps, &p.ctl->wq[level % 3],
               [&](bool valid, int k, int w, int col) {
-    uint32_t vw[G], bm[G];
+    uint32_t vw[G];
+    FwdHit<G, EXT> h;
 #pragma unroll
     for (int g = 0; g < G; g++) {
       vw[g] = 0xffffffffu;
-      bm[g] = 0u;
+      h.bm[g] = 0u;
     }
     bool full = true;
     if (valid) full = load_vis<G>(p, w, vw);
-    int pj = -1;
-    bool hit = false;
+    h.pj = -1;
+    h.hit = false;
     if (valid && !full) {
-      pj = p.ci[col];
-      load_row<G>(Fp, pj, bm);
+      h.pj = p.ci[col];
+      load_row<G>(Fp, h.pj, h.bm);
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        bm[g] &= ~vw[g];
-        hit |= bm[g] != 0u;
+        h.bm[g] &= ~vw[g];
+        h.hit |= h.bm[g] != 0u;
       }
     }
-    int t0 = -1, t1 = -1;
-    const bool sp = hit && two_bits<G>(bm, t0, t1) <= kSparse;
-    unsigned long long s0 = 0ull, s1 = 0ull;
-    bool o0 = false, o1 = false;
-    XS x0, x1;
-    x0.m = x1.m = 0.0;
-    x0.e = x1.e = 0;
-    if (sp) {
-      const size_t i0 = (size_t)pj * (32 * G) + t0;
-      s0 = p.sig[i0];
-      o0 = (p.ovf[(size_t)pj * G + (t0 >> 5)] >> (t0 & 31)) & 1u;
-      if (t1 >= 0) {
-        const size_t i1 = (size_t)pj * (32 * G) + t1;
-        s1 = p.sig[i1];
-        o1 = (p.ovf[(size_t)pj * G + (t1 >> 5)] >> (t1 & 31)) & 1u;
-      }
-      if (EXT) {
-        if (o0) {
-          x0.m = p.xm[i0];
-          x0.e = p.xe[i0];
-        } else {
-          x0 = xs_u64(s0);
-        }
-        if (t1 >= 0) {
-          const size_t i1 = (size_t)pj * (32 * G) + t1;
-          if (o1) {
-            x1.m = p.xm[i1];
-            x1.e = p.xe[i1];
-          } else {
-            x1 = xs_u64(s1);
-          }
-        }
-      }
-    }
+    fwd_hit_load<G, EXT>(p, h);
     const unsigned vm = __ballot_sync(BC_FULL, valid);
-    const unsigned sps = __ballot_sync(BC_FULL, sp);
-    const unsigned dns = __ballot_sync(BC_FULL, hit && !sp);
+    const unsigned sps = __ballot_sync(BC_FULL, h.sp);
+    const unsigned dns = __ballot_sync(BC_FULL, h.hit && !h.sp);
     if (!(sps | dns)) return;
     const int k_lo = __shfl_sync(BC_FULL, k, __ffs(sps | dns) - 1);
     const int k_hi = __shfl_sync(BC_FULL, k, 31 - __clz(sps | dns));
     for (int kk = k_lo; kk <= k_hi; kk++) {
       const unsigned lanes_k = __ballot_sync(BC_FULL, valid && k == kk) & vm;
-      unsigned hs = sps & lanes_k, hd = dns & lanes_k;
+      const unsigned hs = sps & lanes_k, hd = dns & lanes_k;
       if (!(hs | hd)) continue;
       const int jl = __ffs(hs | hd) - 1;
       const int wk = __shfl_sync(BC_FULL, w, jl);
@@ -706,70 +807,7 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
         for (int g = 0; g < G; g++) visc[g] = __shfl_sync(BC_FULL, vw[g], jl);
         pull_init(a);
       }
-      while (hs) {
-        const int jj = __ffs(hs) - 1;
-        hs &= hs - 1;
-        const int u0 = __shfl_sync(BC_FULL, t0, jj), u1 = __shfl_sync(BC_FULL, t1, jj);
-        XS y0, y1;
-        y0.m = y1.m = 0.0;
-        y0.e = y1.e = 0;
-        if (EXT) {
-          y0.m = __shfl_sync(BC_FULL, x0.m, jj);
-          y0.e = __shfl_sync(BC_FULL, x0.e, jj);
-        }
-        pull_sparse_add<G, EXT>(a, u0, __shfl_sync(BC_FULL, s0, jj), __shfl_sync(BC_FULL, o0, jj), y0);
-        if (u1 >= 0) {
-          if (EXT) {
-            y1.m = __shfl_sync(BC_FULL, x1.m, jj);
-            y1.e = __shfl_sync(BC_FULL, x1.e, jj);
-          }
-          pull_sparse_add<G, EXT>(a, u1, __shfl_sync(BC_FULL, s1, jj), __shfl_sync(BC_FULL, o1, jj), y1);
-        }
-      }
-      if (EXT) {
-        while (hd) {
-          const int jj = __ffs(hd) - 1;
-          hd &= hd - 1;
-          uint32_t m[G];
-#pragma unroll
-          for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, bm[g], jj);
-          pull_hit<G, EXT>(p, __shfl_sync(BC_FULL, pj, jj), m, a);
-        }
-      } else {
-        // up to HB<G>::value hits at a time: all their sigma-row loads are issued before any sum
-        while (hd) {
-          unsigned long long sv[HB<G>::value][G];
-          uint32_t mq[HB<G>::value][G];
-          uint32_t povf[HB<G>::value];
-#pragma unroll
-          for (int q = 0; q < HB<G>::value; q++) {
-            const int jq = hd ? __ffs(hd) - 1 : -1;
-            if (hd) hd &= hd - 1;
-            const int pn = __shfl_sync(BC_FULL, pj, jq < 0 ? 0 : jq);
-            povf[q] = 0u;
-#pragma unroll
-            for (int g = 0; g < G; g++) {
-              const uint32_t m = __shfl_sync(BC_FULL, bm[g], jq < 0 ? 0 : jq);
-              mq[q][g] = jq < 0 ? 0u : m;
-              sv[q][g] = 0ull;
-              if ((mq[q][g] >> lane) & 1u) {
-                sv[q][g] = p.sig[(size_t)pn * (32 * G) + 32 * g + lane];
-                if ((p.ovf[(size_t)pn * G + g] >> lane) & 1u) povf[q] |= 1u << g;
-              }
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < HB<G>::value; q++) {
-#pragma unroll
-            for (int g = 0; g < G; g++) {
-              a.newm[g] |= mq[q][g];
-              const unsigned long long old = a.s[g];
-              a.s[g] = old + sv[q][g];
-              if (a.s[g] < old || ((povf[q] >> g) & 1u)) a.o |= 1u << g;
-            }
-          }
-        }
-      }
+      fwd_hits_add<G, EXT>(p, h, hs, hd, a);
     }
   });
   if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
@@ -793,26 +831,22 @@ __device__ bool pull_hub_cta(const TK &p, int w, int level, bool leaf,
   const int lo = min(e1, e0 + wid * per), hi = min(e1, lo + per);
   for (int base = lo; base < hi; base += 32) {
     const int jdx = base + lane;
-    const int pj = jdx < hi ? p.ci[jdx] : -1;
-    uint32_t fm[G];
-    bool hit = false;
-    if (pj >= 0) {
-      load_row<G>(Fp, pj, fm);
+    FwdHit<G, EXT> h;
+    h.pj = jdx < hi ? p.ci[jdx] : -1;
+    h.hit = false;
+    if (h.pj >= 0) {
+      load_row<G>(Fp, h.pj, h.bm);
     } else {
 #pragma unroll
-      for (int g = 0; g < G; g++) fm[g] = 0u;
+      for (int g = 0; g < G; g++) h.bm[g] = 0u;
     }
 #pragma unroll
-    for (int g = 0; g < G; g++) hit |= (fm[g] & ~visw[g]) != 0u;
-    unsigned hits = __ballot_sync(BC_FULL, hit);
-    while (hits) {
-      const int jj = __ffs(hits) - 1;
-      hits &= hits - 1;
-      uint32_t m[G];
-#pragma unroll
-      for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, fm[g], jj) & ~visw[g];
-      pull_hit<G, EXT>(p, __shfl_sync(BC_FULL, pj, jj), m, a);
+    for (int g = 0; g < G; g++) {
+      h.bm[g] &= ~visw[g];
+      h.hit |= h.bm[g] != 0u;
     }
+    fwd_hit_load<G, EXT>(p, h);
+    fwd_hits_add<G, EXT>(p, h, __ballot_sync(BC_FULL, h.sp), __ballot_sync(BC_FULL, h.hit && !h.sp), a);
   }
   unsigned long long *ss = (unsigned long long *)smem;  // [32 warps][32]
   double *sxm = (double *)(ss + kMaxWarps * 32);       // [32][32]
@@ -1463,49 +1497,117 @@ __device__ __forceinline__ void bwd_commit(const TK &p, int w, const BwdOwner<G,
   }
 }
 
+// One backward edge per lane: successor v and the owner's sources bm whose level-(d+1)
+// mask it shares; hits of at most kSparse sources carry their own r values.
+template <int G, bool EXT>
+struct BwdHit {
+  int v;
+  uint32_t bm[G];
+  bool hit, sp;
+  int t0, t1;
+  float2 r0, r1;
+  int e0, e1;
+};
+
+template <int G, bool EXT>
+__device__ __forceinline__ void bwd_hit_load(const TK &p, BwdHit<G, EXT> &h) {
+  h.t0 = h.t1 = -1;
+  h.sp = h.hit && two_bits<G>(h.bm, h.t0, h.t1) <= kSparse;
+  h.r0 = h.r1 = make_float2(0.0f, 0.0f);
+  h.e0 = h.e1 = 0;
+  if (!h.sp) return;
+  const size_t i0 = (size_t)h.v * (32 * G) + h.t0;
+  h.r0 = p.r[i0];
+  if (EXT) h.e0 = p.xe[i0];
+  if (h.t1 >= 0) {
+    const size_t i1 = (size_t)h.v * (32 * G) + h.t1;
+    h.r1 = p.r[i1];
+    if (EXT) h.e1 = p.xe[i1];
+  }
+}
+
+// Add the hits of lanes hs (sparse) and hd (the others), all of one owner, to o.acc.
+template <int G, bool EXT>
+__device__ __forceinline__ void bwd_hits_add(const TK &p, const BwdHit<G, EXT> &h, unsigned hs, unsigned hd,
+                                             BwdOwner<G, EXT> &o) {
+  const int lane = lane_id();
+  while (hs) {
+    const int jj = __ffs(hs) - 1;
+    hs &= hs - 1;
+#pragma unroll
+    for (int z = 0; z < 2; z++) {
+      const int t = __shfl_sync(BC_FULL, z ? h.t1 : h.t0, jj);
+      const float2 x = ff_shfl(z ? h.r1 : h.r0, jj);
+      const int xe = EXT ? __shfl_sync(BC_FULL, z ? h.e1 : h.e0, jj) : 0;
+#pragma unroll
+      for (int g = 0; g < G; g++)
+        if (t >= 0 && (t >> 5) == g && lane == (t & 31)) ff_add(o.acc[g], EXT ? ff_scale(x, o.ew[g] - xe) : x);
+    }
+  }
+  if (EXT) {
+    while (hd) {
+      const int jj = __ffs(hd) - 1;
+      hd &= hd - 1;
+      uint32_t m[G];
+#pragma unroll
+      for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, h.bm[g], jj);
+      bwd_hit<G, EXT>(p, __shfl_sync(BC_FULL, h.v, jj), m, o);
+    }
+    return;
+  }
+  // up to HB<G>::value successors at a time: their r-row loads are in flight together
+  while (hd) {
+    float2 xq[HB<G>::value][G];
+    uint32_t mq[HB<G>::value][G];
+#pragma unroll
+    for (int q = 0; q < HB<G>::value; q++) {
+      const int jj = hd ? __ffs(hd) - 1 : -1;
+      if (hd) hd &= hd - 1;
+      const int vq = __shfl_sync(BC_FULL, h.v, jj < 0 ? 0 : jj);
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        const uint32_t m = __shfl_sync(BC_FULL, h.bm[g], jj < 0 ? 0 : jj);
+        mq[q][g] = jj < 0 ? 0u : m;
+        xq[q][g] = ((mq[q][g] >> lane) & 1u) ? p.r[(size_t)vq * (32 * G) + 32 * g + lane] : make_float2(0.0f, 0.0f);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < HB<G>::value; q++)
+#pragma unroll
+      for (int g = 0; g < G; g++)
+        if (mq[q][g]) ff_add(o.acc[g], xq[q][g]);
+  }
+}
+
 // Backward walk over A_d (hubs skipped): every entry is committed once, in entry order,
 // with the r values of its successors summed: first the sparse hits (loaded by their edge
 // lanes), then the other hits (r rows gathered by the source lanes), each in edge order.
 template <int G, bool EXT>
 __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn, int gwarp,
-                         int nwarps, int *ctr) {
+                         int nwarps, unsigned long long *ctr) {
   int cur = -1;
-  const int lane = lane_id();
   BwdOwner<G, EXT> o;
   walk<true>(p, p.A, p.ACD, a0, a1, E, gwarp, nwarps, ctr, [&](bool valid, int k, int, int col) {
-    uint32_t bm[G];
-    bool hit = false;
-    int v = -1;
+    BwdHit<G, EXT> h;
+    h.hit = false;
+    h.v = -1;
 #pragma unroll
-    for (int g = 0; g < G; g++) bm[g] = 0u;
+    for (int g = 0; g < G; g++) h.bm[g] = 0u;
     if (valid) {
-      v = p.ci[col];
+      h.v = p.ci[col];
       uint32_t am[G];
-      load_row<G>(Dn, v, bm);
+      load_row<G>(Dn, h.v, h.bm);
       load_row<G>(p.AM, k, am);
 #pragma unroll
       for (int g = 0; g < G; g++) {
-        bm[g] &= am[g];
-        hit |= bm[g] != 0u;
+        h.bm[g] &= am[g];
+        h.hit |= h.bm[g] != 0u;
       }
     }
-    int t0 = -1, t1 = -1;
-    const bool sp = hit && two_bits<G>(bm, t0, t1) <= kSparse;
-    float2 r0 = make_float2(0.0f, 0.0f), r1 = make_float2(0.0f, 0.0f);
-    int e0 = 0, e1 = 0;
-    if (sp) {
-      const size_t i0 = (size_t)v * (32 * G) + t0;
-      r0 = p.r[i0];
-      if (EXT) e0 = p.xe[i0];
-      if (t1 >= 0) {
-        const size_t i1 = (size_t)v * (32 * G) + t1;
-        r1 = p.r[i1];
-        if (EXT) e1 = p.xe[i1];
-      }
-    }
+    bwd_hit_load<G, EXT>(p, h);
     const unsigned vm = __ballot_sync(BC_FULL, valid);
-    const unsigned sps = __ballot_sync(BC_FULL, sp);
-    const unsigned dns = __ballot_sync(BC_FULL, hit && !sp);
+    const unsigned sps = __ballot_sync(BC_FULL, h.sp);
+    const unsigned dns = __ballot_sync(BC_FULL, h.hit && !h.sp);
     if (!vm) return;
     const int k_lo = __shfl_sync(BC_FULL, k, __ffs(vm) - 1);
     const int k_hi = __shfl_sync(BC_FULL, k, 31 - __clz(vm));
@@ -1517,54 +1619,7 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
         cur = kk;
         bwd_start<G, EXT>(p, kk, o);
       }
-      unsigned hs = sps & lanes_k, h = dns & lanes_k;
-      while (hs) {
-        const int jj = __ffs(hs) - 1;
-        hs &= hs - 1;
-#pragma unroll
-        for (int z = 0; z < 2; z++) {
-          const int t = __shfl_sync(BC_FULL, z ? t1 : t0, jj);
-          const float2 x = ff_shfl(z ? r1 : r0, jj);
-          const int xe = EXT ? __shfl_sync(BC_FULL, z ? e1 : e0, jj) : 0;
-#pragma unroll
-          for (int g = 0; g < G; g++)
-            if (t >= 0 && (t >> 5) == g && lane == (t & 31)) ff_add(o.acc[g], EXT ? ff_scale(x, o.ew[g] - xe) : x);
-        }
-      }
-      if (EXT) {
-        while (h) {
-          const int jj = __ffs(h) - 1;
-          h &= h - 1;
-          uint32_t m[G];
-#pragma unroll
-          for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, bm[g], jj);
-          bwd_hit<G, EXT>(p, __shfl_sync(BC_FULL, v, jj), m, o);
-        }
-      } else {
-        // up to HB<G>::value successors at a time: their r-row loads are in flight together
-        while (h) {
-          float2 xq[HB<G>::value][G];
-          uint32_t mq[HB<G>::value][G];
-#pragma unroll
-          for (int q = 0; q < HB<G>::value; q++) {
-            const int jj = h ? __ffs(h) - 1 : -1;
-            if (h) h &= h - 1;
-            const int vq = __shfl_sync(BC_FULL, v, jj < 0 ? 0 : jj);
-#pragma unroll
-            for (int g = 0; g < G; g++) {
-              const uint32_t m = __shfl_sync(BC_FULL, bm[g], jj < 0 ? 0 : jj);
-              mq[q][g] = jj < 0 ? 0u : m;
-              xq[q][g] = ((mq[q][g] >> lane) & 1u) ? p.r[(size_t)vq * (32 * G) + 32 * g + lane]
-                                                   : make_float2(0.0f, 0.0f);
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < HB<G>::value; q++)
-#pragma unroll
-            for (int g = 0; g < G; g++)
-              if (mq[q][g]) ff_add(o.acc[g], xq[q][g]);
-        }
-      }
+      bwd_hits_add<G, EXT>(p, h, sps & lanes_k, dns & lanes_k, o);
     }
   });
   if (cur >= 0) bwd_commit<G, EXT>(p, p.A[cur], o);
@@ -1581,26 +1636,22 @@ __device__ void bwd_hub_cta(const TK &p, int k, const uint32_t *Dn, unsigned cha
   const int lo = min(e1, e0 + wid * per), hi = min(e1, lo + per);
   for (int base = lo; base < hi; base += 32) {
     const int jdx = base + lane;
-    const int v = jdx < hi ? p.ci[jdx] : -1;
-    uint32_t dm[G];
-    bool hit = false;
-    if (v >= 0) {
-      load_row<G>(Dn, v, dm);
+    BwdHit<G, EXT> h;
+    h.v = jdx < hi ? p.ci[jdx] : -1;
+    h.hit = false;
+    if (h.v >= 0) {
+      load_row<G>(Dn, h.v, h.bm);
     } else {
 #pragma unroll
-      for (int g = 0; g < G; g++) dm[g] = 0u;
+      for (int g = 0; g < G; g++) h.bm[g] = 0u;
     }
 #pragma unroll
-    for (int g = 0; g < G; g++) hit |= (dm[g] & o.mw[g]) != 0u;
-    unsigned hits = __ballot_sync(BC_FULL, hit);
-    while (hits) {
-      const int jj = __ffs(hits) - 1;
-      hits &= hits - 1;
-      uint32_t m[G];
-#pragma unroll
-      for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, dm[g], jj) & o.mw[g];
-      bwd_hit<G, EXT>(p, __shfl_sync(BC_FULL, v, jj), m, o);
+    for (int g = 0; g < G; g++) {
+      h.bm[g] &= o.mw[g];
+      h.hit |= h.bm[g] != 0u;
     }
+    bwd_hit_load<G, EXT>(p, h);
+    bwd_hits_add<G, EXT>(p, h, __ballot_sync(BC_FULL, h.sp), __ballot_sync(BC_FULL, h.hit && !h.sp), o);
   }
   float2 *sa = (float2 *)smem;
 #pragma unroll 1
