@@ -52,7 +52,8 @@ namespace bcl {
 namespace {
 
 constexpr int kMaxWarps = 32;       // CTA reduction scratch is sized for 1024 threads
-constexpr int kHub = 2048;          // degree from which a vertex is processed by a whole CTA
+constexpr int kHub = 2048;          // degree from which a vertex is processed by whole CTAs
+constexpr int kHubChunk = 4096;     // edges of a hub per backward work item
 constexpr int kLevelsPerChunk = 8;  // levels per launched chunk / captured graph
 constexpr int BCD_NEEDEXT = 4;      // device code: rerun the tile in extended mode
 
@@ -108,7 +109,11 @@ struct TileWS {
   uint32_t *AM = nullptr;
   int32_t *Aoff = nullptr;
   unsigned long long *Lbits = nullptr;
-  int32_t *HE = nullptr, *HEoff = nullptr;  // hub entries of A (positions), per-level offsets
+  int32_t *HE = nullptr, *HEoff = nullptr;  // hub work items (A positions), per-level offsets
+  int32_t *HEk = nullptr, *Hdone = nullptr;  // item's chunk number; chunks done per hub entry
+  float2 *Hpart = nullptr;                   // per-item partial sums (one level's items)
+  int64_t hpart_items = 0;
+  size_t bytes_hpart = 0;
   int32_t *C = nullptr, *CPD = nullptr, *Ch = nullptr;
   float2 *wsrc = nullptr;
   TileCtl *ctl = nullptr;
@@ -143,6 +148,8 @@ struct TK {
   int32_t *Aoff;
   unsigned long long *Lbits;  // per level l: total number of sources over the entries of A_l
   int32_t *HE, *HEoff;
+  int32_t *HEk, *Hdone;  // backward hub items: chunk number; finished chunks of the entry
+  float2 *Hpart;         // [items of a level][T] partial r sums of hub chunks
   int32_t *C, *CPD, *Ch;
   const int32_t *hubs, *Lbu, *PDbu;
   int nhubs, nbu, Ebu;
@@ -222,10 +229,18 @@ __device__ __forceinline__ void append_A(const TK &p, unsigned long long *ctr, i
     if (pos < p.capA) {
       p.A[pos] = v;
       p.ACD[pos] = (int)(b & 0xffffffffull) + pre;
-      if (deg >= kHub) {  // hubs are also listed for the backward sweep
-        const int hp = atomicAdd(&p.ctl->hecnt, 1);
-        if (hp < p.capA) p.HE[hp] = (int)pos;
-        else atomicCAS(&p.ctl->bar.err, 0, BCD_CAPACITY);
+      if (deg >= kHub) {  // hubs are also listed for the backward sweep, one item per chunk
+        const int nch = (deg + kHubChunk - 1) / kHubChunk;
+        const int hp = atomicAdd(&p.ctl->hecnt, nch);
+        if ((long long)hp + nch <= p.capA) {
+          for (int c = 0; c < nch; c++) {
+            p.HE[hp + c] = (int)pos;
+            p.HEk[hp + c] = c;
+          }
+          p.Hdone[hp] = 0;
+        } else {
+          atomicCAS(&p.ctl->bar.err, 0, BCD_CAPACITY);
+        }
       }
     } else {
       atomicCAS(&p.ctl->bar.err, 0, BCD_CAPACITY);
@@ -1626,12 +1641,14 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
 }
 
 template <int G, bool EXT>
-__device__ void bwd_hub_cta(const TK &p, int k, const uint32_t *Dn, unsigned char *smem) {
+__device__ void bwd_hub_item(const TK &p, int i, int h0, const uint32_t *Dn, unsigned char *smem) {
   const int lane = lane_id(), wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int k = p.HE[i], c = p.HEk[i];
   const int w = p.A[k];
+  const int nch = (vdeg(p, w) + kHubChunk - 1) / kHubChunk;
   BwdOwner<G, EXT> o;
   bwd_start<G, EXT>(p, k, o);
-  const int e0 = p.rp[w], e1 = p.rp[w + 1];
+  const int e0 = p.rp[w] + c * kHubChunk, e1 = min(p.rp[w + 1], e0 + kHubChunk);
   const int per = ((e1 - e0 + nw - 1) / nw + 31) & ~31;
   const int lo = min(e1, e0 + wid * per), hi = min(e1, lo + per);
   for (int base = lo; base < hi; base += 32) {
@@ -1665,7 +1682,33 @@ __device__ void bwd_hub_cta(const TK &p, int k, const uint32_t *Dn, unsigned cha
       o.acc[g] = sum;
     }
   }
-  if (wid == 0) bwd_commit<G, EXT>(p, w, o);
+  if (wid == 0) {
+    if (nch == 1) {
+      bwd_commit<G, EXT>(p, w, o);
+    } else {
+      // chunk partials of the entry; the CTA finishing its last chunk sums them in chunk
+      // order (deterministic) and commits
+      float2 *part = p.Hpart + (size_t)(i - h0) * (32 * G);
+#pragma unroll
+      for (int g = 0; g < G; g++)
+        if (o.mw[g]) __stcg(&part[32 * g + lane], o.acc[g]);
+      __threadfence();
+      int last = 0;
+      if (lane == 0) last = atomicAdd(&p.Hdone[i - c], 1) == nch - 1;
+      if (__shfl_sync(BC_FULL, last, 0)) {
+        __threadfence();
+        const float2 *p0 = p.Hpart + (size_t)(i - c - h0) * (32 * G);
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+          if (!o.mw[g]) continue;
+          float2 sum = make_float2(0.0f, 0.0f);
+          for (int cc = 0; cc < nch; cc++) ff_add(sum, __ldcg(&p0[(size_t)cc * (32 * G) + 32 * g + lane]));
+          o.acc[g] = sum;
+        }
+        bwd_commit<G, EXT>(p, w, o);
+      }
+    }
+  }
   __syncthreads();
 }
 
@@ -1842,7 +1885,7 @@ __device__ void phase_bwd_level(const TK &p, int d, int a0, int a1, int Ed, int 
     bwd_lanes<G, EXT>(p, a0, a1, Dn, gwarp, nwarps);
   else
     bwd_walk<G, EXT>(p, a0, a1, Ed, Dn, gwarp, nwarps, &p.ctl->bq[d % 3]);
-  // hub entries of A_d (listed at append time), one per CTA from a shared counter
+  // hub items of A_d (listed at append time, one per chunk), one per CTA from a counter
   __shared__ int s_item;
   const int h0 = p.HEoff[d], h1 = p.HEoff[d + 1];
   int *ctr = &p.ctl->bhubq[d % 3];
@@ -1852,7 +1895,7 @@ __device__ void phase_bwd_level(const TK &p, int d, int a0, int a1, int Ed, int 
     __syncthreads();
     const int i = h0 + s_item;
     if (i >= h1) break;
-    bwd_hub_cta<G, EXT>(p, p.HE[i], Dn, smem);
+    bwd_hub_item<G, EXT>(p, i, h0, Dn, smem);
   }
 }
 
@@ -2149,6 +2192,13 @@ bc_status set_attrs(int G, bool ext) {
 
 // ================================================================== host side
 static void ws_release(Ctx *ctx, TileWS *ws, bool main, bool ext, bool A) {
+  if (main && ws->Hpart) {
+    cudaFree(ws->Hpart);
+    ctx->mem.release(nullptr, ws->bytes_hpart);
+    ws->Hpart = nullptr;
+    ws->hpart_items = 0;
+    ws->bytes_hpart = 0;
+  }
   if (main && ws->ctl) {
     void *ptrs[] = {ws->vis, ws->F, ws->ovf, ws->cand, ws->sig, ws->r, ws->Aoff, ws->Lbits, ws->HEoff,
                     ws->C, ws->CPD, ws->Ch, ws->wsrc, ws->ctl};
@@ -2177,7 +2227,9 @@ static void ws_release(Ctx *ctx, TileWS *ws, bool main, bool ext, bool A) {
     cudaFree(ws->ACD);
     cudaFree(ws->AM);
     cudaFree(ws->HE);
-    ws->HE = nullptr;
+    cudaFree(ws->HEk);
+    cudaFree(ws->Hdone);
+    ws->HE = ws->HEk = ws->Hdone = nullptr;
     ctx->mem.release(nullptr, ws->bytes_A);
     ws->A = ws->ACD = nullptr;
     ws->AM = nullptr;
@@ -2269,25 +2321,52 @@ static bc_status ws_ext(Ctx *ctx, TileWS *ws) {
 static bc_status ws_A(Ctx *ctx, TileWS *ws, int64_t cap) {
   if (ws->A && ws->capA >= cap) return BC_OK;
   ws_release(ctx, ws, false, false, true);
-  const size_t bytes = (size_t)cap * (12 + 4 * ws->G);
+  const size_t bytes = (size_t)cap * (20 + 4 * ws->G);
   bc_status s = ctx->mem.alloc(nullptr, bytes);
   if (s) return s;
   cudaError_t e = cudaSuccess;
   TA(ws->A, (size_t)cap * 4);
   TA(ws->ACD, (size_t)cap * 4);
   TA(ws->HE, (size_t)cap * 4);
+  TA(ws->HEk, (size_t)cap * 4);
+  TA(ws->Hdone, (size_t)cap * 4);
   TA(ws->AM, (size_t)cap * 4 * ws->G);
   if (e != cudaSuccess) {
     cudaGetLastError();
     ctx->mem.release(nullptr, bytes);
-    if (ws->A) cudaFree(ws->A);
-    if (ws->ACD) cudaFree(ws->ACD);
-    if (ws->HE) cudaFree(ws->HE);
-    ws->A = ws->ACD = ws->HE = nullptr;
+    void *ptrs[] = {ws->A, ws->ACD, ws->HE, ws->HEk, ws->Hdone, ws->AM};
+    for (void *q : ptrs)
+      if (q) cudaFree(q);
+    ws->A = ws->ACD = ws->HE = ws->HEk = ws->Hdone = nullptr;
+    ws->AM = nullptr;
     return fail(BC_ENOMEM, "tile active-list allocation failed");
   }
   ws->capA = cap;
   ws->bytes_A = bytes;
+  return BC_OK;
+}
+
+// Partial sums of the backward hub chunks of one level: a level lists each hub at most
+// once, so it has at most nnz / kHubChunk + (number of hubs) items.
+static bc_status ws_hpart(Ctx *ctx, TileWS *ws, int64_t nnz) {
+  const int64_t items = nnz / kHubChunk + ws->nhubs + 16;
+  if (ws->Hpart && ws->hpart_items >= items) return BC_OK;
+  if (ws->Hpart) {
+    cudaFree(ws->Hpart);
+    ctx->mem.release(nullptr, ws->bytes_hpart);
+    ws->Hpart = nullptr;
+  }
+  const size_t bytes = (size_t)items * ws->T * sizeof(float2);
+  bc_status s = ctx->mem.alloc(nullptr, bytes);
+  if (s) return s;
+  if (cudaMalloc((void **)&ws->Hpart, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ws->Hpart = nullptr;
+    ctx->mem.release(nullptr, bytes);
+    return fail(BC_ENOMEM, "tile hub-partials allocation failed");
+  }
+  ws->hpart_items = items;
+  ws->bytes_hpart = bytes;
   return BC_OK;
 }
 
@@ -2506,6 +2585,7 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
   TileWS *ws = *wsp;
   bc_status s = ws_main(ctx, ws, dg->n, a.T);
   if (!s) s = ws_lists(ctx, ws, dg, st);
+  if (!s) s = ws_hpart(ctx, ws, dg->nnz);
   if (s) return s;
   const int G = a.T / 32;
   if (!ws->A) {
@@ -2554,6 +2634,9 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
       p.Lbits = ws->Lbits;
       p.HE = ws->HE;
       p.HEoff = ws->HEoff;
+      p.HEk = ws->HEk;
+      p.Hdone = ws->Hdone;
+      p.Hpart = ws->Hpart;
       p.C = ws->C;
       p.CPD = ws->CPD;
       p.Ch = ws->Ch;

@@ -146,6 +146,26 @@ def test_tile_hubs_exact(ctx):
     bc.bc_destroy(h)
 
 
+def test_tile_hub_chunks_exact(ctx):
+    """Hubs of degree 10,000 and 9,000 (three chunks each, spread over CTAs, partial sums
+    combined by the last chunk) plus a sparse part, at both tile widths and loop modes."""
+    rng = np.random.Generator(np.random.PCG64(12))
+    n = 14000
+    e = [(0, i) for i in range(1, 10001)] + [(10001, i) for i in range(4000, 13001)]
+    u = rng.integers(0, n, 9000)
+    v = rng.integers(0, n, 9000)
+    e += list(zip(u.tolist(), v.tolist()))
+    g = gg.from_edge_list(n, e)
+    h = upload(ctx, g)
+    src = np.arange(3, g.n, 211, dtype=np.int32)
+    want = oracle.bc(g, src, nthreads=8)
+    for T in (64, 256):
+        for mode in (0, bc.BC_LOOP_LAUNCH):
+            got, _ = bc.bc_sources(h, g.n, src, TILED | bc.BC_TILE(T) | mode)
+            assert_bc_close(got, want, what=f"hub chunks T={T} mode={mode}")
+    bc.bc_destroy(h)
+
+
 def test_tile_duplicates_and_plain_agree(ctx):
     g = gg.rmat(11, 8, 4)
     h = upload(ctx, g)
