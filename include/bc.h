@@ -57,6 +57,10 @@ enum {
 #define BC_PATH_TILED     (1u << 4)  /* force the multi-source tile path                */
 #define BC_LOOP_LAUNCH    (1u << 5)  /* tile path: one kernel launch per level phase    */
 #define BC_LOOP_GRAPH     (1u << 6)  /* tile path: level loop replayed as a CUDA graph  */
+#define BC_PLAIN_GRID     (1u << 7)  /* per-source path: always the grid-wide kernel     */
+/* (by default the per-source path runs graphs of up to 65,536 vertices one source per CTA,
+ *  all SMs on different sources; larger graphs use the grid-wide kernel, one source at a
+ *  time over the whole GPU) */
 /* bits 8..11: tile width selector for BC_PATH_TILED: 0 = autotuned, else 32 << (k-1) */
 #define BC_TILE_SHIFT     8
 #define BC_TILE_MASK      (0xFu << BC_TILE_SHIFT)
@@ -105,9 +109,10 @@ bc_status bc_exact(bc_graph *g, uint32_t flags, double *bc_out, void *cuda_strea
 bc_status bc_sources(bc_graph *g, const int32_t *src, int32_t k, uint32_t flags,
                      double *bc_out, void *cuda_stream, bc_stats *stats);
 
-/* Single-source shortest-path counting (Alg. 2 / Alg. 3) on the per-source path:
- * depth[n] (-1 = unreached), sigma[n] = number of shortest paths modulo 2^64, and
- * sigma_ovf[n] = 1 where the true count is >= 2^64.  Host buffers unless
+/* Single-source shortest-path counting (Alg. 2 / Alg. 3) on the per-source path (one CTA
+ * for graphs of up to 65,536 vertices, the grid-wide kernel above that or with
+ * BC_PLAIN_GRID): depth[n] (-1 = unreached), sigma[n] = number of shortest paths modulo
+ * 2^64, and sigma_ovf[n] = 1 where the true count is >= 2^64.  Host buffers unless
  * BC_DEVICE_PTRS. */
 bc_status bc_sssp(bc_graph *g, int32_t s, uint32_t flags, int32_t *depth, uint64_t *sigma,
                   uint8_t *sigma_ovf);

@@ -207,8 +207,6 @@ bc_status run_sources(Graph *g, const int32_t *d_src, int32_t k, uint32_t flags,
     (void)leaf_term;
     return BC_OK;
   }
-  bc_status s = plain_ensure(ctx, &g->plain, dg->n);
-  if (s) return s;
   PlainArgs pa{};
   pa.g = dg;
   pa.omega = omega;
@@ -219,6 +217,9 @@ bc_status run_sources(Graph *g, const int32_t *d_src, int32_t k, uint32_t flags,
   pa.max_degree = g->max_degree;
   pa.alpha = alpha;
   pa.beta = beta;
+  if (cta_fits(dg->n) && !(flags & BC_PLAIN_GRID)) return cta_run(ctx, g, &g->cta, pa, st, stats);
+  bc_status s = plain_ensure(ctx, &g->plain, dg->n);
+  if (s) return s;
   return plain_run(ctx, &g->plain, pa, st, stats);
 }
 
@@ -470,7 +471,8 @@ bc_status bc_sssp(bc_graph *graph, int32_t s, uint32_t flags, int32_t *depth, ui
   std::lock_guard<std::mutex> lk(g->mu);
   cudaStream_t st = c->own_stream;
   const size_t n = (size_t)g->g.n;
-  bc_status r = plain_ensure(c, &g->plain, g->g.n);
+  const bool cta = cta_fits(g->g.n) && !(flags & BC_PLAIN_GRID);
+  bc_status r = cta ? BC_OK : plain_ensure(c, &g->plain, g->g.n);
   if (r) return r;
   // one scratch block carved at 16-byte aligned offsets: sigma | depth | ovf | src
   const size_t o_dep = align16(n * 8), o_ovf = o_dep + align16(n * 4),
@@ -495,7 +497,11 @@ bc_status bc_sssp(bc_graph *graph, int32_t s, uint32_t flags, int32_t *depth, ui
   pa.alpha = g->tune.ready ? g->tune.res.alpha : 0.5f;
   pa.beta = g->tune.ready ? g->tune.res.beta : 24.f;
   pa.bc = nullptr;
-  r = plain_run(c, &g->plain, pa, st, nullptr);
+  if (cta) {
+    r = cta_run(c, g, &g->cta, pa, st, nullptr);
+  } else {
+    r = plain_run(c, &g->plain, pa, st, nullptr);
+  }
   if (r) return r;
   cudaMemcpyKind kind = (flags & BC_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   BC_CUDA_TRY(cudaMemcpyAsync(depth, d_dep, n * 4, kind, st));
@@ -597,6 +603,10 @@ static void graph_free(Graph *g) {
   Ctx *c = g->ctx;
   plain_free(c, &g->plain);
   prune_free(c, &g->prune);
+  if (g->cta) {
+    cta_free(c, g->cta);
+    g->cta = nullptr;
+  }
   if (g->tile) {
     tile_free(c, g->tile);
     g->tile = nullptr;

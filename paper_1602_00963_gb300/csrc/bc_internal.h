@@ -85,6 +85,7 @@ struct DeviceGraph {
 };
 
 struct TileWS;  // bc_tile.cu
+struct CtaWS;   // bc_cta.cu
 
 struct PruneCache {
   bool ready = false;
@@ -115,6 +116,7 @@ struct Graph {
   PruneCache prune;
   TuneCache tune;
   TileWS *tile = nullptr;  // tile-path workspace (bc_tile.cu)
+  CtaWS *cta = nullptr;    // per-source path on small graphs (bc_cta.cu)
   std::vector<int32_t> h_deg_nonisolated;  // host copy for sampled requests
 };
 
@@ -153,6 +155,14 @@ void plain_free(Ctx *ctx, PlainWS *ws);
 bc_status plain_run(Ctx *ctx, PlainWS *ws, const PlainArgs &a, cudaStream_t st, bc_stats *acc);
 bc_status plain_run_view(const PlainWS &ws, const PlainArgs &a, int num_sms, uint64_t limit_ns,
                          cudaStream_t st, int *dev_err);
+
+// ---- per-source path on small graphs: one CTA per source (bc_cta.cu)
+constexpr int32_t kCtaMaxN = 65536;
+bool cta_fits(int32_t n);
+// Runs a.src, one source per CTA (a.out_depth set: forward only for a.src[0], depth / sigma /
+// overflow exported).
+bc_status cta_run(Ctx *ctx, Graph *g, CtaWS **ws, const PlainArgs &a, cudaStream_t st, bc_stats *acc);
+void cta_free(Ctx *ctx, CtaWS *ws);
 
 // ---- device 1-degree preprocessing (bc_prune.cu)
 bc_status prune_build(Ctx *ctx, Graph *g, cudaStream_t st);

@@ -11,6 +11,9 @@
 //     dependencies are routed to its own request's accumulator);
 //   * run the tile with per-phase launches (not the cooperative kernel) so that tiles of
 //     different graphs, on different streams, overlap on the device;
+//   * on small graphs (up to 65,536 vertices) instead run one request's remaining sources
+//     on the per-source CTA kernel (each CTA a source at a time, all SMs busy), which
+//     there is far faster than a tile;
 //   * complete a request when its last tile is done: copy its BC to the caller's buffer.
 // A request that arrives while others run is admitted as soon as memory allows and its
 // sources join the next tiles of its graph.
@@ -55,6 +58,9 @@ struct Req {
 struct GraphExec {
   Graph *g = nullptr;
   TileWS *ws = nullptr;
+  CtaWS *cta = nullptr;        // small graphs: per-source CTA kernel workspace
+  int32_t *d_many = nullptr;   // its source list
+  size_t cap_many = 0;
   int32_t *d_src = nullptr;
   uint8_t *d_lane = nullptr;
   double **d_reqbc = nullptr;
@@ -86,7 +92,17 @@ int tile_width_for(Graph *g) {
 
 size_t tile_ws_estimate(Graph *g, int T) {
   const size_t n = (size_t)g->g.n, G = (size_t)T / 32;
+  if (cta_fits(g->g.n)) return n * 64;  // CTA kernel: it shrinks its partials to the budget
   return n * G * 20 + n * T * 16 + n * (20 + 12 * G) * 4;
+}
+
+void exec_release(Ctx *c, GraphExec *e) {
+  if (e->ws) tile_free(c, e->ws);
+  if (e->cta) cta_free(c, e->cta);
+  if (e->d_many) c->mem.release(e->d_many, e->cap_many * 4);
+  if (e->d_src) c->mem.release(e->d_src, 256 * 4);
+  if (e->d_lane) c->mem.release(e->d_lane, 256);
+  if (e->d_reqbc) c->mem.release(e->d_reqbc, kMaxReqPerTile * sizeof(double *));
 }
 
 void finish(Server *sv, Req *r, bc_status st) {
@@ -180,6 +196,53 @@ void worker_main(Server *sv, int wid) {
       continue;
     }
     Graph *g = job->g;
+    if (cta_fits(g->g.n)) {
+      // small graph: the remaining sources of its first unscheduled request, one launch
+      Req *r = nullptr;
+      for (Req *q : sv->active)
+        if (q->g == g && !q->canceled && q->next < q->src.size()) {
+          r = q;
+          break;
+        }
+      const size_t k = r->src.size() - r->next;
+      hsrc.assign(r->src.begin() + (long)r->next, r->src.end());
+      r->next = r->src.size();
+      r->inflight++;
+      if (!r->started) {
+        r->started = true;
+        r->t_start = Clock::now();
+        r->queue_s = std::chrono::duration<double>(r->t_start - r->t_submit).count();
+      }
+      job->busy = true;
+      job->counted = true;
+      lk.unlock();
+      bc_status s = BC_OK;
+      if (job->cap_many < k) {
+        if (job->d_many) c->mem.release(job->d_many, job->cap_many * 4);
+        job->d_many = nullptr;
+        job->cap_many = 0;
+        s = c->mem.alloc((void **)&job->d_many, k * 4);
+        if (!s) job->cap_many = k;
+      }
+      if (!s && cudaMemcpyAsync(job->d_many, hsrc.data(), k * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        s = fail(BC_ECUDA, "serving: copy of request sources");
+      if (!s) {
+        PlainArgs pa{};
+        pa.g = &g->g;
+        pa.src = job->d_many;
+        pa.nsrc = (int32_t)k;
+        pa.bc = r->d_bc;
+        pa.max_degree = g->max_degree;
+        s = cta_run(c, g, &job->cta, pa, st, nullptr);
+      }
+      lk.lock();
+      job->busy = false;
+      r->inflight--;
+      if (s && r->status == BC_OK) r->status = s;
+      if (r->inflight == 0) finish(sv, r, r->status);
+      sv->cv_work.notify_all();
+      continue;
+    }
     const int T = tile_width_for(g);
     hsrc.clear();
     hlane.clear();
@@ -285,12 +348,8 @@ void server_stop(Ctx *c) {
     delete r;
   }
   for (auto &kv : sv->gx) {
-    GraphExec *e = kv.second;
-    if (e->ws) tile_free(c, e->ws);
-    if (e->d_src) c->mem.release(e->d_src, 256 * 4);
-    if (e->d_lane) c->mem.release(e->d_lane, 256);
-    if (e->d_reqbc) c->mem.release(e->d_reqbc, kMaxReqPerTile * sizeof(double *));
-    delete e;
+    exec_release(c, kv.second);
+    delete kv.second;
   }
   delete sv;
 }
@@ -320,10 +379,7 @@ void server_forget_graph(Ctx *c, Graph *g) {
   auto it = sv->gx.find(g);
   if (it == sv->gx.end()) return;
   GraphExec *e = it->second;
-  if (e->ws) tile_free(c, e->ws);
-  if (e->d_src) c->mem.release(e->d_src, 256 * 4);
-  if (e->d_lane) c->mem.release(e->d_lane, 256);
-  if (e->d_reqbc) c->mem.release(e->d_reqbc, kMaxReqPerTile * sizeof(double *));
+  exec_release(c, e);
   delete e;
   sv->gx.erase(it);
   for (auto it2 = sv->reqs.begin(); it2 != sv->reqs.end();) {  // finished, unpolled results

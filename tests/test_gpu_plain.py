@@ -1,5 +1,7 @@
 """Parity of the per-source CUDA path (bc_sssp, bc_exact, bc_sources with
-BC_PATH_PLAIN) against the CPU oracle, through the C ABI."""
+BC_PATH_PLAIN) against the CPU oracle, through the C ABI.  Each test runs both kernels of
+the path: one CTA per source (the default on these small graphs) and the grid-wide kernel
+(BC_PLAIN_GRID)."""
 import numpy as np
 import pytest
 
@@ -20,6 +22,11 @@ def ctx():
     bc.bc_destroy(c)
 
 
+@pytest.fixture(params=[0, bc.BC_PLAIN_GRID], ids=["cta", "grid"])
+def kern(request):
+    return request.param
+
+
 SMALL = [
     gg.path_graph(2), gg.path_graph(17), gg.star_graph(9), gg.complete_graph(7),
     gg.cycle_graph(10), gg.cycle_graph(11), gg.complete_bipartite(3, 5), gg.hypercube(5),
@@ -29,51 +36,51 @@ SMALL = [
 
 
 @pytest.mark.parametrize("gi", range(len(SMALL)))
-def test_small_exact(ctx, gi):
+def test_small_exact(ctx, gi, kern):
     g = SMALL[gi]
     h = upload(ctx, g)
-    got, st = bc.bc_exact(h, g.n, PLAIN)
+    got, st = bc.bc_exact(h, g.n, PLAIN | kern)
     assert_bc_close(got, oracle.bc_exact(g), what=g.name)
-    got, _ = bc.bc_exact(h, g.n, PLAIN | bc.BC_PRUNE_DEG1)
+    got, _ = bc.bc_exact(h, g.n, PLAIN | kern | bc.BC_PRUNE_DEG1)
     assert_bc_close(got, oracle.bc_exact(g), what=g.name + " pruned")
     bc.bc_destroy(h)
 
 
-def test_sssp_rmat(ctx):
+def test_sssp_rmat(ctx, kern):
     g = gg.rmat(12, 16, 1)
     h = upload(ctx, g)
     for s in [0, 5, 77, 1000, 4095]:
-        assert_sssp_equal(bc.bc_sssp(h, g.n, s), oracle.sssp(g, s), f"rmat12 s={s}")
+        assert_sssp_equal(bc.bc_sssp(h, g.n, s, kern), oracle.sssp(g, s), f"rmat12 s={s}")
     bc.bc_destroy(h)
 
 
-def test_sssp_grid_overflow(ctx):
+def test_sssp_grid_overflow(ctx, kern):
     """48x48 open grid: counts pass 2^64 beyond distance ~67; sigma mod 2^64 and the
     overflow flags must match bit for bit."""
     g = gg.grid2d(48, 48)
     h = upload(ctx, g)
     for s in [0, 17 * 48 + 30, 48 * 48 - 1]:
-        got = bc.bc_sssp(h, g.n, s)
+        got = bc.bc_sssp(h, g.n, s, kern)
         want = oracle.sssp(g, s)
         assert want[2].any() or s != 0
         assert_sssp_equal(got, want, f"grid48 s={s}")
     bc.bc_destroy(h)
 
 
-def test_sssp_ba_and_deleted_grid(ctx):
+def test_sssp_ba_and_deleted_grid(ctx, kern):
     for g in [gg.ba_pref_attach(3000, 9), gg.grid2d(64, 64, seed=5, delete_frac=0.1)]:
         h = upload(ctx, g)
         rng = np.random.Generator(np.random.PCG64(1))
         for s in rng.choice(g.n, 6, replace=False):
-            assert_sssp_equal(bc.bc_sssp(h, g.n, int(s)), oracle.sssp(g, int(s)), f"{g.name} s={s}")
+            assert_sssp_equal(bc.bc_sssp(h, g.n, int(s), kern), oracle.sssp(g, int(s)), f"{g.name} s={s}")
         bc.bc_destroy(h)
 
 
-def test_exact_rmat12_all_sources(ctx):
+def test_exact_rmat12_all_sources(ctx, kern):
     """R-MAT scale 12, edge factor 16, seed 1, all sources, no pruning, no batching."""
     g = gg.rmat(12, 16, 1)
     h = upload(ctx, g)
-    got, st = bc.bc_exact(h, g.n, PLAIN)
+    got, st = bc.bc_exact(h, g.n, PLAIN | kern)
     want = oracle.bc_exact(g, nthreads=8)
     assert_bc_close(got, want, what="rmat12 exact")
     assert st["sources"] == int((g.degrees() > 0).sum())
@@ -82,29 +89,32 @@ def test_exact_rmat12_all_sources(ctx):
     bc.bc_destroy(h)
 
 
-def test_exact_grid_extended_sigma(ctx):
+def test_exact_grid_extended_sigma(ctx, kern):
     """Grid with deletions: sigma overflows 2^64 and FP64; delta uses the extended-range
-    sigma.  All sources of a 40x40 grid (10% deleted, largest component)."""
+    sigma.  All sources of a
+    40x40 grid (10% deleted, largest component); four sources of an open 120x120 grid (CTA
+    state in global memory)."""
     g = gg.grid2d(40, 40, seed=5, delete_frac=0.1)
     h = upload(ctx, g)
-    got, st = bc.bc_exact(h, g.n, PLAIN)
+    got, st = bc.bc_exact(h, g.n, PLAIN | kern)
     assert_bc_close(got, oracle.bc_exact(g, nthreads=8), what="grid40 exact")
     bc.bc_destroy(h)
     g = gg.grid2d(120, 120)
     h = upload(ctx, g)
     src = np.array([0, 119, 60 * 120 + 60, 120 * 120 - 1], np.int32)
-    got, st = bc.bc_sources(h, g.n, src, PLAIN)
+    got, st = bc.bc_sources(h, g.n, src, PLAIN | kern)
     assert st["sigma_overflow_sources"] == 4
+    assert st["sources"] == 4
     assert_bc_close(got, oracle.bc(g, src), what="grid120 sources")
     bc.bc_destroy(h)
 
 
-def test_pruned_ba(ctx):
+def test_pruned_ba(ctx, kern):
     g = gg.ba_pref_attach(4000, 2)
     h = upload(ctx, g)
     want = oracle.bc_exact(g, nthreads=8)
-    got_p, st_p = bc.bc_exact(h, g.n, PLAIN | bc.BC_PRUNE_DEG1)
-    got_u, st_u = bc.bc_exact(h, g.n, PLAIN)
+    got_p, st_p = bc.bc_exact(h, g.n, PLAIN | kern | bc.BC_PRUNE_DEG1)
+    got_u, st_u = bc.bc_exact(h, g.n, PLAIN | kern)
     assert_bc_close(got_p, want, what="ba pruned")
     assert_bc_close(got_u, want, what="ba unpruned")
     assert st_p["sources"] < st_u["sources"]
@@ -122,18 +132,18 @@ def test_device_prune_matches_oracle(ctx):
         bc.bc_destroy(h)
 
 
-def test_sources_multiset_and_device_ptrs(ctx):
+def test_sources_multiset_and_device_ptrs(ctx, kern):
     torch = pytest.importorskip("torch")
     g = gg.rmat(10, 8, 3)
     h = upload(ctx, g)
     src = np.array([3, 3, 17, 500, 1023, 3], np.int32)
     want = oracle.bc(g, src)
-    got, st = bc.bc_sources(h, g.n, src, PLAIN)
+    got, st = bc.bc_sources(h, g.n, src, PLAIN | kern)
     assert st["sources"] == 6
     assert_bc_close(got, want, what="multiset host")
     dsrc = torch.from_numpy(src).cuda()
     dout = torch.zeros(g.n, dtype=torch.float64, device="cuda")
-    bc.bc_sources(h, g.n, dsrc, PLAIN, bc_out=dout)
+    bc.bc_sources(h, g.n, dsrc, PLAIN | kern, bc_out=dout)
     assert_bc_close(dout.cpu().numpy(), want, what="multiset device")
     bc.bc_destroy(h)
 
@@ -158,17 +168,20 @@ def test_invalid_inputs(ctx):
 
 
 def test_wait_limit_timeout_then_recovery(ctx):
-    """A zero device-wait limit makes the first grid barrier give up: the call returns
-    BC_ETIMEDOUT (no hang, no fault) and the context stays usable."""
+    """A zero device-wait limit makes the first grid barrier of the grid-wide kernel give
+    up: the call returns BC_ETIMEDOUT (no hang, no fault) and the context stays usable.
+    (The CTA kernel has no inter-CTA waits.)"""
     g = gg.rmat(10, 8, 5)
     h = upload(ctx, g)
     bc.bc_set_wait_limit_ms(ctx, 0)
     try:
         with pytest.raises(bc.BCError) as e:
-            bc.bc_exact(h, g.n, PLAIN)
+            bc.bc_exact(h, g.n, PLAIN | bc.BC_PLAIN_GRID)
         assert e.value.status == bc.BC_ETIMEDOUT
+        got, _ = bc.bc_exact(h, g.n, PLAIN)  # the CTA kernel is unaffected
+        assert_bc_close(got, oracle.bc_exact(g), what="CTA kernel under a zero wait limit")
     finally:
         bc.bc_set_wait_limit_ms(ctx, 20000)
-    got, _ = bc.bc_exact(h, g.n, PLAIN)
+    got, _ = bc.bc_exact(h, g.n, PLAIN | bc.BC_PLAIN_GRID)
     assert_bc_close(got, oracle.bc_exact(g), what="after timeout")
     bc.bc_destroy(h)
