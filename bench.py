@@ -58,12 +58,17 @@ def parse():
 def profile_case(spec: str):
     """One bc_sources call, for ncu captures of a single kernel: on the R-MAT scale-20 graph
     ('tile:T:K', 'plain:K') or on the 1024 x 1024 deleted-edge grid ('grid:T:K'; its
-    sigma needs the extended range, so the tile runs twice when it starts in 64-bit mode)."""
+    sigma needs the extended range, so the tile runs twice when it starts in 64-bit mode),
+    or the per-source path on R-MAT scale 12 with its first K non-isolated sources
+    ('small:K', one source per CTA)."""
     import paper_1602_00963_gb300 as bc
     parts = spec.split(":")
     if parts[0] == "grid":
         g = gg.cached("grid", gg.grid2d, 1024, 1024, 5, 0.1)
         src = gg.sample_sources(g, 1024, seed=6)
+    elif parts[0] == "small":
+        g = gg.rmat(12, 16, 1)
+        src = np.flatnonzero(g.degrees() > 0).astype(np.int32)
     else:
         g, src = load_workload(4096, 0)
     ctx = bc.bc_ctx_create(0)
@@ -74,6 +79,8 @@ def profile_case(spec: str):
     else:
         k = int(parts[1])
         flags = bc.BC_PATH_PLAIN
+    if parts[0] == "small":
+        bc.bc_sources(h, g.n, src[:k], flags)  # warm-up: workspace and shared-memory setup
     _, st = bc.bc_sources(h, g.n, src[:k], flags)
     print(json.dumps({"profile_case": spec, "seconds": st["seconds"], "gteps": st["gteps"],
                       "kernel_launches": st["kernel_launches"],
