@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sources", type=int, default=4096)
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--study", default=None, choices=["deg1"],
+                    help="deg1: the 1-degree removal study on R-MAT scale 20, EF 4 / 16 / 32 "
+                         "(one JSON line, instead of the benchmark)")
     ap.add_argument("--profile-case", default=None,
                     help="run one small case for a profiler and exit: 'tile:T:K' (one bc_sources "
                          "call of K sources in tiles of T) or 'plain:K' on the R-MAT scale-20 graph")
@@ -269,7 +272,7 @@ def serving_pool():
     ]
 
 
-def serving_bench(bc, ctx, rates=(0.5, 1.0, 2.0), window_s=12.0, seed=100):
+def serving_bench(bc, ctx, rates=(0.5, 1.0, 2.0, 4.0, 8.0), window_s=8.0, seed=100):
     """Poisson arrivals of BC requests over the resident pool at each rate: graph uniform,
     k = floor(exp(U(0, ln 1024))) sources, exact list or sampled with probability 1/2.
     Reports p50 / p99 of the latency (submit -> result) and the delivered GTEPS."""
@@ -359,12 +362,59 @@ def grid_loop_bench(bc, ctx, T: int = 64):
     return out
 
 
+# ------------------------------------------------------------------ 1-degree study
+def deg1_study(scale: int = 20, efs=(4, 16, 32), k: int = 1024, T: int = 64):
+    """1-degree removal (Eq. 3 / Eq. 4, Alg. 6) on R-MAT graphs of one scale and several edge
+    factors (seed 3): preprocessing time (device pruning plus the copies of omega and the
+    residual CSR to the host), then the mean time per source of the tile path on the original
+    graph (k sources drawn from the non-isolated vertices) and on the residual graph (k
+    drawn from the residual vertices), and totals extrapolated to every source of each run,
+    as the paper's totals are (the pruned run has fewer sources and fewer edges)."""
+    import paper_1602_00963_gb300 as bc
+    ctx = bc.bc_ctx_create(0)
+    flags = bc.BC_PATH_TILED | bc.BC_TILE(T)
+    rows = []
+    for ef in efs:
+        g = gg.cached("rmat", gg.rmat, scale, ef, 3)
+        h = bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0)
+        bc.bc_prune(h, g.n, g.nnz)  # warm-up
+        t = time.perf_counter()
+        om, rem, rrp, rci = bc.bc_prune(h, g.n, g.nnz)
+        t_pre = time.perf_counter() - t
+        hr = bc.bc_graph_create(ctx, g.n, rrp, rci, rci.size, 0)
+        deg = g.degrees()
+        all_src = np.flatnonzero(deg > 0)
+        res_src = np.flatnonzero((deg > 0) & (rem == 0))
+        rng = np.random.Generator(np.random.PCG64(5))
+        su = rng.choice(all_src, size=min(k, all_src.size), replace=False).astype(np.int32)
+        sp = rng.choice(res_src, size=min(k, res_src.size), replace=False).astype(np.int32)
+        bc.bc_sources(h, g.n, su[:T], flags)
+        bc.bc_sources(hr, g.n, sp[:T], flags)
+        _, stu = bc.bc_sources(h, g.n, su, flags)
+        _, stp = bc.bc_sources(hr, g.n, sp, flags)
+        per_u, per_p = stu["seconds"] / su.size, stp["seconds"] / sp.size
+        tot_u, tot_p = per_u * all_src.size, per_p * res_src.size + t_pre
+        rows.append({"edge_factor": ef, "n": g.n, "m": g.m, "leaves_removed": int(rem.sum()),
+                     "sources_unpruned": int(all_src.size), "sources_pruned": int(res_src.size),
+                     "residual_m": int(rci.size // 2), "preprocessing_s": t_pre,
+                     "mean_ms_per_source_unpruned": per_u * 1e3, "mean_ms_per_source_pruned": per_p * 1e3,
+                     "total_s_unpruned": tot_u, "total_s_pruned": tot_p, "speedup": tot_u / tot_p})
+        bc.bc_destroy(hr)
+        bc.bc_destroy(h)
+    bc.bc_destroy(ctx)
+    print(json.dumps({"study": "1-degree removal, R-MAT scale %d (seed 3), tiles of %d, %d sampled sources" % (scale, T, k),
+                      "rows": rows}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.profile_case:
         profile_case(args.profile_case)
+        return
+    if args.study == "deg1":
+        deg1_study()
         return
     if args.impl == "reference":
         if world > 1:
