@@ -59,8 +59,8 @@ constexpr int kLevelsPerChunk = 8;  // levels per launched chunk / captured grap
 constexpr int BCD_NEEDEXT = 4;      // device code: rerun the tile in extended mode
 
 template <int G>
-struct TPB {  // threads per CTA: wide tiles keep more state per lane
-  static constexpr int value = G >= 4 ? 512 : 1024;
+struct TPB {  // threads per CTA (one CTA per SM): 256-wide tiles keep more state per lane
+  static constexpr int value = G >= 8 ? 768 : 1024;
 };
 // hits whose row gathers are in flight together (fewer for wide tiles, whose rows already
 // issue G loads per hit)
