@@ -25,7 +25,7 @@ __all__ = [
     "Graph", "csr_from_edges", "rmat", "ba_pref_attach", "grid2d", "erdos_renyi",
     "largest_component", "component_labels", "sample_sources", "from_edge_list",
     "path_graph", "star_graph", "complete_graph", "cycle_graph", "complete_bipartite",
-    "hypercube", "random_tree", "gnm", "cached",
+    "hypercube", "random_tree", "gnm", "cached", "subdivide_edges",
 ]
 
 
@@ -184,6 +184,19 @@ def grid2d(w: int, h: int, seed: int | None = None, delete_frac: float = 0.0,
         g, _ = largest_component(g)
         g.name = name + "-lcc"
     return g
+
+
+def subdivide_edges(g: Graph, frac: float, seed: int) -> Graph:
+    """Road-network shape: a seeded fraction of the edges (u, v) become paths u - x - v
+    through a new degree-2 vertex x (ids n, n + 1, ... in edge order)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    src, dst = g.edges()
+    pick = rng.random(src.size) < frac
+    k = int(pick.sum())
+    x = g.n + np.arange(k, dtype=np.int64)
+    s2 = np.concatenate([src[~pick], src[pick], x])
+    d2 = np.concatenate([dst[~pick], x, dst[pick]])
+    return csr_from_edges(g.n + k, s2, d2, f"{g.name}-sub{frac}-seed{seed}")
 
 
 # ------------------------------------------------------------------- Erdos-Renyi
