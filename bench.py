@@ -49,9 +49,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sources", type=int, default=4096)
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
-    ap.add_argument("--study", default=None, choices=["deg1"],
-                    help="deg1: the 1-degree removal study on R-MAT scale 20, EF 4 / 16 / 32 "
-                         "(one JSON line, instead of the benchmark)")
+    ap.add_argument("--study", default=None, choices=["deg1", "deg2"],
+                    help="deg1: the 1-degree removal study on R-MAT scale 20, EF 4 / 16 / 32; "
+                         "deg2: the 2-degree heuristic on road-like graphs (one JSON line, "
+                         "instead of the benchmark)")
     ap.add_argument("--profile-case", default=None,
                     help="run one small case for a profiler and exit: 'tile:T:K' (one bc_sources "
                          "call of K sources in tiles of T) or 'plain:K' on the R-MAT scale-20 graph")
@@ -406,6 +407,52 @@ def deg1_study(scale: int = 20, efs=(4, 16, 32), k: int = 1024, T: int = 64):
                       "rows": rows}), flush=True)
 
 
+def deg2_triples(g) -> int:
+    """How many degree-2 runs the library derives: degree-2 vertices c taken in vertex
+    order while c and both neighbours are unused (the rule of BC_DEG2)."""
+    used = np.zeros(g.n, bool)
+    cnt = 0
+    for c in np.flatnonzero(g.degrees() == 2):
+        a, b = g.col_idx[g.row_ptr[c]:g.row_ptr[c] + 2]
+        if used[c] or used[a] or used[b]:
+            continue
+        used[[a, b, c]] = True
+        cnt += 1
+    return cnt
+
+
+def deg2_study():
+    """2-degree heuristic (Sec. 3.4.2) on road-network stand-ins small enough for the
+    per-source CTA kernel: all sources, exact BC with and without the heuristic (device
+    time of the call), the number of degree-2 runs derived, and the largest relative
+    difference between the two results."""
+    import paper_1602_00963_gb300 as bc
+    ctx = bc.bc_ctx_create(0)
+    graphs = [("grid 256x256, 10% deleted, LCC", gg.cached("grid", gg.grid2d, 256, 256, 16, 0.1)),
+              ("grid 160x160, 10% deleted, LCC, 40% of edges subdivided",
+               gg.subdivide_edges(gg.grid2d(160, 160, seed=18, delete_frac=0.1), 0.4, 19))]
+    rows = []
+    P = bc.BC_PATH_PLAIN
+    for name, g in graphs:
+        h = bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0)
+        bc.bc_sources(h, g.n, gg.sample_sources(g, 64, seed=1), P)  # workspace set-up
+        bc.bc_exact(h, g.n, P | bc.BC_DEG2)
+        b0, s0 = bc.bc_exact(h, g.n, P)
+        b2, s2 = bc.bc_exact(h, g.n, P | bc.BC_DEG2)
+        deg = g.degrees()
+        ntri = deg2_triples(g)
+        err = np.abs(b2 - b0) / np.maximum(np.abs(b0), 1.0)
+        rows.append({"graph": name, "n": g.n, "m": g.m, "degree2_vertices": int((deg == 2).sum()),
+                     "derived_runs": ntri, "sources": int((deg > 0).sum()),
+                     "seconds_plain": s0["seconds"], "seconds_deg2": s2["seconds"],
+                     "speedup": s0["seconds"] / s2["seconds"], "gteps_plain": s0["gteps"],
+                     "gteps_deg2": s2["gteps"], "max_rel_diff": float(err.max())})
+        bc.bc_destroy(h)
+    bc.bc_destroy(ctx)
+    print(json.dumps({"study": "2-degree heuristic, per-source path (one source per CTA), all sources",
+                      "rows": rows}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -415,6 +462,9 @@ def main():
         return
     if args.study == "deg1":
         deg1_study()
+        return
+    if args.study == "deg2":
+        deg2_study()
         return
     if args.impl == "reference":
         if world > 1:

@@ -61,6 +61,13 @@ enum {
 /* (by default the per-source path runs graphs of up to 65,536 vertices one source per CTA,
  *  all SMs on different sources; larger graphs use the grid-wide kernel, one source at a
  *  time over the whole GPU) */
+/* bc_exact: 2-degree heuristic (Sec. 3.4.2).  A set of degree-2 vertices c, no two sharing
+ * a neighbour or being one, is run without a traversal of its own: the shortest-path DAG of c
+ * is derived from those of its two neighbours a, b (run from the same CTA) and c's
+ * dependencies are accumulated on it (dynamic merging of frontiers, Alg. 8 / Alg. 9).  The
+ * result equals the plain run.  Per-source path on graphs of up to 65,536 vertices only;
+ * not with BC_PRUNE_DEG1, BC_PATH_TILED or BC_PLAIN_GRID (BC_EINVAL). */
+#define BC_DEG2           (1u << 12)
 /* bits 8..11: tile width selector for BC_PATH_TILED: 0 = autotuned, else 32 << (k-1) */
 #define BC_TILE_SHIFT     8
 #define BC_TILE_MASK      (0xFu << BC_TILE_SHIFT)

@@ -362,6 +362,47 @@ static bc_status full_source_list(Graph *g, const DeviceGraph *dg, int32_t **lis
   return BC_OK;
 }
 
+// 2-degree heuristic (Sec. 3.4.2): pick degree-2 vertices c with neighbours a, b, in vertex
+// order, such that no vertex belongs to two triples; each triple runs a and b and derives c
+// (one CTA), every other non-isolated vertex runs as usual.
+static bc_status run_deg2(Graph *g, double *d_bc, cudaStream_t st, bc_stats *acc) {
+  Ctx *c = g->ctx;
+  const int32_t n = g->g.n;
+  std::vector<int32_t> rp((size_t)n + 1), ci((size_t)g->g.nnz);
+  BC_CUDA_TRY(cudaMemcpy(rp.data(), g->g.rp, rp.size() * 4, cudaMemcpyDeviceToHost));
+  if (!ci.empty()) BC_CUDA_TRY(cudaMemcpy(ci.data(), g->g.ci, ci.size() * 4, cudaMemcpyDeviceToHost));
+  std::vector<uint8_t> used((size_t)n, 0);
+  std::vector<int32_t> tri, single;
+  for (int32_t v = 0; v < n; v++) {
+    if (rp[v + 1] - rp[v] != 2) continue;
+    const int32_t a = ci[rp[v]], b = ci[rp[v] + 1];
+    if (used[v] || used[a] || used[b]) continue;
+    used[v] = used[a] = used[b] = 1;
+    tri.push_back(a);
+    tri.push_back(b);
+    tri.push_back(v);
+  }
+  for (int32_t v = 0; v < n; v++)
+    if (rp[v + 1] > rp[v] && !used[v]) single.push_back(v);
+  DevBuf sbuf, tbuf;
+  bc_status s = sbuf.get(c, (single.size() + 1) * 4);
+  if (!s) s = tbuf.get(c, (tri.size() + 3) * 4);
+  if (s) return s;
+  if (!single.empty())
+    BC_CUDA_TRY(cudaMemcpyAsync(sbuf.p, single.data(), single.size() * 4, cudaMemcpyHostToDevice, st));
+  if (!tri.empty())
+    BC_CUDA_TRY(cudaMemcpyAsync(tbuf.p, tri.data(), tri.size() * 4, cudaMemcpyHostToDevice, st));
+  PlainArgs pa{};
+  pa.g = &g->g;
+  pa.src = (const int32_t *)sbuf.p;
+  pa.nsrc = (int32_t)single.size();
+  pa.tri = (const int32_t *)tbuf.p;
+  pa.ntri = (int32_t)(tri.size() / 3);
+  pa.bc = d_bc;
+  pa.max_degree = g->max_degree;
+  return cta_run(c, g, &g->cta, pa, st, acc);
+}
+
 static void finish_stats(Graph *g, bc_stats *acc, bc_stats *out) {
   if (!out) return;
   acc->edges = g->g.nnz / 2;
@@ -388,7 +429,12 @@ bc_status bc_exact(bc_graph *graph, uint32_t flags, double *bc_out, void *cuda_s
   BC_CUDA_TRY(cudaMemsetAsync(d_bc, 0, (size_t)n * 8, st));
   bc_stats acc{};
   bc_status s;
-  if (flags & BC_PRUNE_DEG1) {
+  if (flags & BC_DEG2) {
+    if (flags & (BC_PRUNE_DEG1 | BC_PATH_TILED | BC_PLAIN_GRID))
+      return fail(BC_EINVAL, "bc_exact: BC_DEG2 runs on the per-source CTA kernel only, unpruned");
+    if (!cta_fits(n)) return fail(BC_EINVAL, "bc_exact: BC_DEG2 needs a graph of at most 65,536 vertices");
+    s = run_deg2(g, d_bc, st, &acc);
+  } else if (flags & BC_PRUNE_DEG1) {
     s = prune_build(c, g, st);
     if (s) return s;
     s = run_sources(g, g->prune.src, g->prune.nsrc, flags, g->prune.omega, true, d_bc, st, &acc,

@@ -48,6 +48,8 @@ struct CtaK {
   int in_smem;        // state arrays in shared memory
   unsigned long long *stats;  // reached pairs, their arcs, levels, deepest level (max),
                               // sources whose sigma passed 2^64
+  const int32_t *tri;         // 2-degree triples (a, b, c), 3 ints each
+  int ntri;
   int32_t *out_depth;         // forward-only export of src[0] (sssp), or null
   unsigned long long *out_sigma;
   uint8_t *out_ovf;
@@ -60,197 +62,334 @@ struct CtaK {
 __host__ __device__ inline size_t cta_state_bytes(int n) {
   return ((size_t)n * 24 + ((size_t)(n + 31) / 32) * 4 + 16 + 15) & ~(size_t)15;
 }
-__host__ __device__ inline size_t cta_extra_bytes(int n) {
-  return ((size_t)(n + 2) * 4 + 15) / 16 * 16 + (size_t)n * 12;
+__host__ __device__ inline size_t cta_extra_bytes(int n) {  // a multiple of 16: states follow
+  return (((size_t)(n + 2) * 4 + 15) / 16 * 16 + (size_t)n * 12 + 15) & ~(size_t)15;
 }
 
+// One source's state: per-vertex arrays plus the level offsets and extended-range sigma.
+struct CtaState {
+  unsigned long long *sig;
+  float2 *r;
+  int32_t *d;
+  int32_t *Q;
+  uint32_t *ovf;
+  int32_t *loff;
+  double *xm;
+  int32_t *xe;
+};
+
+// Carve a state: the per-vertex block at blk (cta_state_bytes), the rest at extra
+// (cta_extra_bytes).
+__device__ __forceinline__ CtaState cta_carve(char *blk, char *extra, int n) {
+  CtaState S;
+  S.sig = (unsigned long long *)blk;
+  S.r = (float2 *)(blk + (size_t)n * 8);
+  S.d = (int32_t *)(blk + (size_t)n * 16);
+  S.Q = S.d + n;
+  S.ovf = (uint32_t *)(S.Q + n);
+  S.loff = (int32_t *)extra;
+  S.xm = (double *)(extra + ((size_t)(n + 2) * 4 + 15) / 16 * 16);
+  S.xe = (int32_t *)(S.xm + n);
+  return S;
+}
+
+struct CtaShared {
+  int q, ovf, lovf[2];
+  unsigned long long ns;
+};
+
 // sigma of v as m 2^e with m in [0.5, 1)
-__device__ __forceinline__ XS cta_sigma(const unsigned long long *sig, const uint32_t *ovf,
-                                        const double *xm, const int32_t *xe, int v) {
-  if ((ovf[v >> 5] >> (v & 31)) & 1u) {
+__device__ __forceinline__ XS cta_sigma(const CtaState &S, int v) {
+  if ((S.ovf[v >> 5] >> (v & 31)) & 1u) {
     XS x;
-    x.m = xm[v];
-    x.e = xe[v];
+    x.m = S.xm[v];
+    x.e = S.xe[v];
     return x;
   }
-  return xs_u64(sig[v]);
+  return xs_u64(S.sig[v]);
+}
+__device__ __forceinline__ int cta_exp(const CtaState &S, int v) {
+  return ((S.ovf[v >> 5] >> (v & 31)) & 1u) ? S.xe[v] : 64 - __clzll((long long)S.sig[v]);
+}
+
+__device__ void cta_clear(const CtaState &S, int n) {
+  for (int v = threadIdx.x; v < n; v += kCtaThreads) {
+    S.sig[v] = 0ull;
+    S.d[v] = -1;
+  }
+  for (int i = threadIdx.x; i < (n + 31) / 32; i += kCtaThreads) S.ovf[i] = 0u;
+}
+
+// Forward sweep from s (Alg. 2 / Alg. 3, CTA barriers).  Returns the deepest non-empty
+// level; *qtot = reached vertices, *arcs += their adjacency entries (lane 0 of each warp).
+__device__ int cta_forward(const CtaK &p, const CtaState &S, int s, CtaShared &sh, int *qtot,
+                           unsigned long long *arcs) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) {
+    S.d[s] = 0;
+    S.sig[s] = 1ull;
+    S.Q[0] = s;
+    S.loff[0] = 0;
+    S.loff[1] = 1;
+    sh.q = 1;
+    sh.ovf = 0;
+    sh.lovf[1] = 0;
+    sh.ns = 1ull + (p.omega ? (unsigned long long)p.omega[s] : 0ull);
+  }
+  __syncthreads();
+  int level = 1, q0 = 0, q1 = 1;
+  while (q1 > q0) {
+    for (int i = q0 + wid; i < q1; i += kCtaWarps) {
+      const int v = S.Q[i];
+      const unsigned long long sv = S.sig[v];
+      const bool ov = (S.ovf[v >> 5] >> (v & 31)) & 1u;
+      const int e0 = p.rp[v], e1 = p.rp[v + 1];
+      if (lane == 0) *arcs += (unsigned long long)(e1 - e0);
+      for (int e = e0 + lane; e < e1; e += 32) {
+        const int w = p.ci[e];
+        int dw = *(volatile int32_t *)&S.d[w];
+        if (dw < 0) {
+          const int old = atomicCAS(&S.d[w], -1, level);
+          if (old < 0) {
+            S.Q[atomicAdd(&sh.q, 1)] = w;
+            if (p.leaf_term && p.omega) atomicAdd(&sh.ns, 1ull + (unsigned long long)p.omega[w]);
+            dw = level;
+          } else {
+            dw = old;
+          }
+        }
+        if (dw == level) {
+          const unsigned long long old = atomicAdd(&S.sig[w], sv);
+          if (old + sv < old || ov) {
+            atomicOr(&S.ovf[w >> 5], 1u << (w & 31));
+            sh.ovf = 1;
+            sh.lovf[level & 1] = 1;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const int q2 = sh.q;
+    const bool lovf = sh.lovf[level & 1] != 0;
+    if (tid == 0) sh.lovf[(level + 1) & 1] = 0;
+    __syncthreads();
+    if (tid == 0) S.loff[level + 1] = q2;
+    if (lovf) {
+      // extended-range sigma of the overflowed vertices of this level: the sum over the
+      // parents (level - 1), lanes in edge order, then a fixed-order warp reduction
+      for (int i = q1 + wid; i < q2; i += kCtaWarps) {
+        const int w = S.Q[i];
+        if (!((S.ovf[w >> 5] >> (w & 31)) & 1u)) continue;
+        XS acc;
+        acc.m = 0.0;
+        acc.e = 0;
+        const int e1 = p.rp[w + 1];
+        for (int e = p.rp[w] + lane; e < e1; e += 32) {
+          const int v = p.ci[e];
+          if (S.d[v] == level - 1) xs_add(acc, cta_sigma(S, v));
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+          XS o;
+          o.m = __shfl_down_sync(BC_FULL, acc.m, off);
+          o.e = __shfl_down_sync(BC_FULL, acc.e, off);
+          xs_add(acc, o);
+        }
+        if (lane == 0) {
+          acc = xs_norm(acc);
+          S.xm[w] = acc.m;
+          S.xe[w] = acc.e;
+        }
+      }
+      __syncthreads();
+    }
+    q0 = q1;
+    q1 = q2;
+    level++;
+  }
+  *qtot = q1;
+  return level - 2;
+}
+
+// Backward sweep of s (Alg. 4 / Alg. 5): sigma of w taken as m 2^e, r stored scaled by 2^e.
+__device__ void cta_backward(const CtaK &p, const CtaState &S, int s, int lmax, double *bcp,
+                             const CtaShared &sh) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const float2 wsrc = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[s] : 0ull));
+  for (int dd = lmax; dd >= 1; --dd) {
+    const int a0 = S.loff[dd], a1 = S.loff[dd + 1];
+    for (int i = a0 + wid; i < a1; i += kCtaWarps) {
+      const int w = S.Q[i];
+      const XS sw = cta_sigma(S, w);
+      float2 acc = make_float2(0.0f, 0.0f);
+      if (dd < lmax) {
+        const int e1 = p.rp[w + 1];
+        for (int e = p.rp[w] + lane; e < e1; e += 32) {
+          const int v = p.ci[e];
+          if (S.d[v] != dd + 1) continue;
+          ff_add(acc, ff_scale(S.r[v], sw.e - cta_exp(S, v)));
+        }
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) ff_add(acc, ff_shfl_xor(acc, m));
+      }
+      if (lane == 0) {
+        const float2 mw = ff_mant(sw.m);
+        const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
+        float2 rw = ff_mul(om1, ff_rcp(mw));
+        ff_add(rw, acc);
+        S.r[w] = rw;  // r scaled by 2^e of w
+        const float2 dl = ff_mul(wsrc, ff_mul(mw, acc));
+        if (!ff_zero(dl)) bcp[w] += ff_to(dl);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && p.leaf_term && p.omega && p.omega[s] > 0) {
+    const double om = (double)p.omega[s];
+    bcp[s] += om * (2.0 * (double)sh.ns - om - 3.0);
+  }
+}
+
+__device__ void cta_reset(const CtaState &S, int qtot) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < qtot; i += kCtaThreads) {
+    const int w = S.Q[i];
+    S.d[w] = -1;
+    S.sig[w] = 0ull;
+    S.ovf[w >> 5] = 0u;
+  }
+  __syncthreads();
+}
+
+// ---- 2-degree vertex c with neighbours a, b (Sec. 3.4.2): its shortest-path DAG follows
+// from those of a and b.  For v != c: level_c(v) = 1 + min(level_a(v), level_b(v)) and
+// sigma_c(v) = sigma_a(v), sigma_b(v) or their sum as the smaller level comes from a, from b
+// or from both (Eq. in Sec. 3.4.2, by the Bellman criterion); level_c(c) = 0, sigma_c(c) = 1.
+__device__ __forceinline__ int deg2_level(const CtaState &A, const CtaState &B, int c, int v) {
+  if (v == c) return 0;
+  const int da = A.d[v], db = B.d[v];
+  if (da < 0 && db < 0) return -1;
+  if (da < 0) return db + 1;
+  if (db < 0) return da + 1;
+  return (da < db ? da : db) + 1;
+}
+__device__ __forceinline__ XS deg2_sigma(const CtaState &A, const CtaState &B, int c, int v) {
+  if (v == c) return xs_u64(1ull);
+  const int da = A.d[v], db = B.d[v];
+  if (db < 0 || (da >= 0 && da < db)) return cta_sigma(A, v);
+  if (da < 0 || db < da) return cta_sigma(B, v);
+  XS x = cta_sigma(A, v);
+  xs_add(x, cta_sigma(B, v));
+  return xs_norm(x);
+}
+
+// Backward sweep of the 2-degree vertex c on its derived DAG, level by level (the dynamic
+// merging of frontiers, Alg. 8 / Alg. 9): c's level D holds the vertices of a's level D - 1
+// whose level from b is not smaller, and those of b's level D - 1 whose level from a is
+// larger.  rc holds c's r values (scaled by 2^e of sigma_c).  Unpruned graphs only (omega = 0).
+__device__ void cta_backward_deg2(const CtaK &p, const CtaState &A, const CtaState &B, int lmaxA, int lmaxB,
+                                  int c, float2 *rc, double *bcp) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lmax = 1 + (lmaxA > lmaxB ? lmaxA : lmaxB);
+  for (int D = lmax; D >= 1; --D) {
+#pragma unroll 1
+    for (int side = 0; side < 2; side++) {
+      const CtaState &S = side ? B : A;
+      const int lm = side ? lmaxB : lmaxA;
+      if (D - 1 > lm) continue;
+      const int a0 = S.loff[D - 1], a1 = S.loff[D];
+      for (int i = a0 + wid; i < a1; i += kCtaWarps) {
+        const int w = S.Q[i];
+        if (w == c) continue;
+        const int da = A.d[w], db = B.d[w];
+        const bool mine = side == 0 ? (db < 0 || da <= db) : (da < 0 || db < da);
+        if (!mine) continue;
+        const XS sw = deg2_sigma(A, B, c, w);
+        float2 acc = make_float2(0.0f, 0.0f);
+        const int e1 = p.rp[w + 1];
+        for (int e = p.rp[w] + lane; e < e1; e += 32) {
+          const int v = p.ci[e];
+          if (deg2_level(A, B, c, v) != D + 1) continue;
+          ff_add(acc, ff_scale(rc[v], sw.e - deg2_sigma(A, B, c, v).e));
+        }
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) ff_add(acc, ff_shfl_xor(acc, m));
+        if (lane == 0) {
+          const float2 mw = ff_mant(sw.m);
+          float2 rw = ff_rcp(mw);
+          ff_add(rw, acc);
+          rc[w] = rw;
+          const float2 dl = ff_mul(mw, acc);
+          if (!ff_zero(dl)) bcp[w] += ff_to(dl);
+        }
+      }
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void __launch_bounds__(kCtaThreads) k_cta_sources(CtaK p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = p.n;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   char *gslice = p.gws + (size_t)blockIdx.x * p.slice;
-  char *base = p.in_smem ? (char *)smem : gslice;
-  unsigned long long *sig = (unsigned long long *)base;
-  float2 *r = (float2 *)(base + (size_t)n * 8);
-  int32_t *d = (int32_t *)(base + (size_t)n * 16);
-  int32_t *Q = d + n;
-  uint32_t *ovf = (uint32_t *)(Q + n);
-  char *extra = gslice + (p.in_smem ? 0 : cta_state_bytes(n));
-  int32_t *loff = (int32_t *)extra;
-  double *xm = (double *)(extra + ((size_t)(n + 2) * 4 + 15) / 16 * 16);
-  int32_t *xe = (int32_t *)(xm + n);
-  double *bcp = p.bcp + (size_t)blockIdx.x * n;
-
-  __shared__ int s_q, s_ovf, s_lovf[2];
-  __shared__ unsigned long long s_ns;
-
-  for (int v = tid; v < n; v += kCtaThreads) {
-    sig[v] = 0ull;
-    d[v] = -1;
-    bcp[v] = 0.0;
+  const size_t sb = cta_state_bytes(n), xb = cta_extra_bytes(n);
+  // state A: shared memory when it fits; state B and c's r (2-degree triples) after it
+  char *g = gslice;
+  char *blkA = p.in_smem ? (char *)smem : g;
+  if (!p.in_smem) g += sb;
+  const CtaState A = cta_carve(blkA, g, n);
+  g += xb;
+  CtaState B = A;
+  float2 *rc = nullptr;
+  if (p.ntri) {
+    B = cta_carve(g, g + sb, n);
+    rc = (float2 *)(g + sb + xb);
   }
-  for (int i = tid; i < (n + 31) / 32; i += kCtaThreads) ovf[i] = 0u;
+  double *bcp = p.bcp + (size_t)blockIdx.x * n;
+  __shared__ CtaShared sh;
+
+  for (int v = tid; v < n; v += kCtaThreads) bcp[v] = 0.0;
+  cta_clear(A, n);
+  if (p.ntri) cta_clear(B, n);
   unsigned long long my_arcs = 0, my_reached = 0, my_levels = 0, my_deep = 0, my_ovf = 0;
   __syncthreads();
 
+  auto account = [&](int lmax, int qtot) {
+    my_reached += (unsigned long long)qtot;
+    my_levels += (unsigned long long)(lmax + 1);
+    if ((unsigned long long)lmax > my_deep) my_deep = (unsigned long long)lmax;
+    if (sh.ovf) my_ovf++;
+  };
   for (int si = blockIdx.x; si < p.nsrc; si += gridDim.x) {
     const int s = p.src[si];
-    if (tid == 0) {
-      d[s] = 0;
-      sig[s] = 1ull;
-      Q[0] = s;
-      loff[0] = 0;
-      loff[1] = 1;
-      s_q = 1;
-      s_ovf = 0;
-      s_lovf[1] = 0;
-      s_ns = 1ull + (p.omega ? (unsigned long long)p.omega[s] : 0ull);
-    }
-    __syncthreads();
-    // ---------------------------------------------------------------- forward
-    int level = 1, q0 = 0, q1 = 1;
-    unsigned long long src_arcs = 0;
-    while (q1 > q0) {
-      for (int i = q0 + wid; i < q1; i += kCtaWarps) {
-        const int v = Q[i];
-        const unsigned long long sv = sig[v];
-        const bool ov = (ovf[v >> 5] >> (v & 31)) & 1u;
-        const int e0 = p.rp[v], e1 = p.rp[v + 1];
-        if (lane == 0) src_arcs += (unsigned long long)(e1 - e0);
-        for (int e = e0 + lane; e < e1; e += 32) {
-          const int w = p.ci[e];
-          int dw = *(volatile int32_t *)&d[w];
-          if (dw < 0) {
-            const int old = atomicCAS(&d[w], -1, level);
-            if (old < 0) {
-              Q[atomicAdd(&s_q, 1)] = w;
-              if (p.leaf_term && p.omega) atomicAdd(&s_ns, 1ull + (unsigned long long)p.omega[w]);
-              dw = level;
-            } else {
-              dw = old;
-            }
-          }
-          if (dw == level) {
-            const unsigned long long old = atomicAdd(&sig[w], sv);
-            if (old + sv < old || ov) {
-              atomicOr(&ovf[w >> 5], 1u << (w & 31));
-              s_ovf = 1;
-              s_lovf[level & 1] = 1;
-            }
-          }
-        }
-      }
-      __syncthreads();
-      const int q2 = s_q;
-      const bool lovf = s_lovf[level & 1] != 0;
-      if (tid == 0) s_lovf[(level + 1) & 1] = 0;
-      __syncthreads();
-      if (tid == 0) loff[level + 1] = q2;
-      if (lovf) {
-        // extended-range sigma of the overflowed vertices of this level: the sum over the
-        // parents (level - 1), lanes in edge order, then a fixed-order warp reduction
-        for (int i = q1 + wid; i < q2; i += kCtaWarps) {
-          const int w = Q[i];
-          if (!((ovf[w >> 5] >> (w & 31)) & 1u)) continue;
-          XS acc;
-          acc.m = 0.0;
-          acc.e = 0;
-          const int e1 = p.rp[w + 1];
-          for (int e = p.rp[w] + lane; e < e1; e += 32) {
-            const int v = p.ci[e];
-            if (d[v] == level - 1) xs_add(acc, cta_sigma(sig, ovf, xm, xe, v));
-          }
-#pragma unroll
-          for (int off = 16; off >= 1; off >>= 1) {
-            XS o;
-            o.m = __shfl_down_sync(BC_FULL, acc.m, off);
-            o.e = __shfl_down_sync(BC_FULL, acc.e, off);
-            xs_add(acc, o);
-          }
-          if (lane == 0) {
-            acc = xs_norm(acc);
-            xm[w] = acc.m;
-            xe[w] = acc.e;
-          }
-        }
-        __syncthreads();
-      }
-      q0 = q1;
-      q1 = q2;
-      level++;
-    }
-    const int lmax = level - 2;  // deepest non-empty level
-    const int qtot = q1;
-    my_arcs += src_arcs;
-    my_reached += (unsigned long long)qtot;
-    my_levels += (unsigned long long)(level - 1);
-    if ((unsigned long long)lmax > my_deep) my_deep = (unsigned long long)lmax;
-    if (s_ovf) my_ovf++;
-
+    int qtot = 0;
+    const int lmax = cta_forward(p, A, s, sh, &qtot, &my_arcs);
+    account(lmax, qtot);
     if (p.out_depth) {  // forward-only export (sssp of src[0])
       for (int v = tid; v < n; v += kCtaThreads) {
-        p.out_depth[v] = d[v];
-        p.out_sigma[v] = sig[v];
-        p.out_ovf[v] = (uint8_t)((ovf[v >> 5] >> (v & 31)) & 1u);
+        p.out_depth[v] = A.d[v];
+        p.out_sigma[v] = A.sig[v];
+        p.out_ovf[v] = (uint8_t)((A.ovf[v >> 5] >> (v & 31)) & 1u);
       }
     } else {
-      // -------------------------------------------------------------- backward
-      const float2 wsrc = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[s] : 0ull));
-      for (int dd = lmax; dd >= 1; --dd) {
-        const int a0 = loff[dd], a1 = loff[dd + 1];
-        for (int i = a0 + wid; i < a1; i += kCtaWarps) {
-          const int w = Q[i];
-          const XS sw = cta_sigma(sig, ovf, xm, xe, w);
-          float2 acc = make_float2(0.0f, 0.0f);
-          if (dd < lmax) {
-            const int e1 = p.rp[w + 1];
-            for (int e = p.rp[w] + lane; e < e1; e += 32) {
-              const int v = p.ci[e];
-              if (d[v] != dd + 1) continue;
-              const int ev = ((ovf[v >> 5] >> (v & 31)) & 1u) ? xe[v] : 64 - __clzll((long long)sig[v]);
-              ff_add(acc, ff_scale(r[v], sw.e - ev));
-            }
-#pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) ff_add(acc, ff_shfl_xor(acc, m));
-          }
-          if (lane == 0) {
-            const float2 mw = ff_mant(sw.m);
-            const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
-            float2 rw = ff_mul(om1, ff_rcp(mw));
-            ff_add(rw, acc);
-            r[w] = rw;  // r scaled by 2^e of w
-            const float2 dl = ff_mul(wsrc, ff_mul(mw, acc));
-            if (!ff_zero(dl)) bcp[w] += ff_to(dl);
-          }
-        }
-        __syncthreads();
-      }
-      if (tid == 0 && p.leaf_term && p.omega && p.omega[s] > 0) {
-        const double om = (double)p.omega[s];
-        bcp[s] += om * (2.0 * (double)s_ns - om - 3.0);
-      }
+      cta_backward(p, A, s, lmax, bcp, sh);
     }
-    // reset the reached vertices for the next source
-    __syncthreads();
-    for (int i = tid; i < qtot; i += kCtaThreads) {
-      const int w = Q[i];
-      d[w] = -1;
-      sig[w] = 0ull;
-      ovf[w >> 5] = 0u;
-    }
-    __syncthreads();
+    cta_reset(A, qtot);
+  }
+  // 2-degree triples (a, b, c): a and b as usual, c from their two DAGs
+  for (int ti = blockIdx.x; ti < p.ntri; ti += gridDim.x) {
+    const int a = p.tri[3 * ti], b = p.tri[3 * ti + 1], c = p.tri[3 * ti + 2];
+    int qa = 0, qb = 0;
+    const int la = cta_forward(p, A, a, sh, &qa, &my_arcs);
+    account(la, qa);
+    cta_backward(p, A, a, la, bcp, sh);
+    const int lb = cta_forward(p, B, b, sh, &qb, &my_arcs);
+    account(lb, qb);
+    cta_backward(p, B, b, lb, bcp, sh);
+    cta_backward_deg2(p, A, B, la, lb, c, rc, bcp);
+    cta_reset(A, qa);
+    cta_reset(B, qb);
   }
   // statistics
   for (int m = 16; m >= 1; m >>= 1) my_arcs += __shfl_xor_sync(BC_FULL, my_arcs, m);
@@ -275,7 +414,7 @@ __global__ void k_cta_reduce(const double *bcp, int ncta, int n, double *bc) {
 }  // namespace
 
 struct CtaWS {
-  int n = 0, ncta = 0, in_smem = 0;
+  int n = 0, ncta = 0, in_smem = 0, tri = 0;
   size_t slice = 0, smem = 0;
   double *bcp = nullptr;
   char *gws = nullptr;
@@ -292,7 +431,7 @@ void cta_free(Ctx *ctx, CtaWS *ws) {
   delete ws;
 }
 
-static bc_status cta_ensure(Ctx *ctx, CtaWS **wsp, int n) {
+static bc_status cta_ensure(Ctx *ctx, CtaWS **wsp, int n, bool tri) {
   CtaWS *ws = *wsp;
   const size_t st = cta_state_bytes(n);
   const int in_smem = st <= kCtaSmemMax;
@@ -305,7 +444,10 @@ static bc_status cta_ensure(Ctx *ctx, CtaWS **wsp, int n) {
   if (bps < 1) return fail(BC_ECUDA, "CTA per-source kernel does not fit on an SM");
   if (!in_smem) bps = std::min(bps, 2);  // slices live in L2 / HBM: keep their total small
   int ncta = ctx->num_sms * bps;
-  const size_t slice = ((in_smem ? 0 : st) + cta_extra_bytes(n) + 255) & ~(size_t)255;
+  // slice: state A (unless in shared memory) and its extras; with triples also state B,
+  // its extras and c's r values
+  const size_t slice = ((in_smem ? 0 : st) + cta_extra_bytes(n) +
+                        (tri ? st + cta_extra_bytes(n) + (size_t)n * 8 : 0) + 255) & ~(size_t)255;
   const size_t per_cta = (size_t)n * 8 + slice;
   if (ctx->mem.budget) {  // fewer CTAs when the context's HBM budget is tight
     const size_t used = ctx->mem.used.load() - (ws ? ws->bytes : 0);
@@ -313,7 +455,7 @@ static bc_status cta_ensure(Ctx *ctx, CtaWS **wsp, int n) {
     ncta = (int)std::min<size_t>((size_t)ncta, avail / per_cta);
     if (ncta < 1) return fail(BC_ENOMEM, "CTA per-source workspace exceeds the context HBM budget");
   }
-  if (ws && ws->n == n && ws->ncta == ncta) return BC_OK;
+  if (ws && ws->n == n && ws->ncta == ncta && ws->tri >= (int)tri) return BC_OK;
   if (ws) {
     cta_free(ctx, ws);
     *wsp = nullptr;
@@ -324,6 +466,7 @@ static bc_status cta_ensure(Ctx *ctx, CtaWS **wsp, int n) {
   ws->in_smem = in_smem;
   ws->smem = smem;
   ws->slice = slice;
+  ws->tri = tri ? 1 : 0;
   const size_t b_bcp = (size_t)ncta * n * 8, b_gws = ws->slice * ncta;
   ws->bytes = b_bcp + b_gws + 64;
   bc_status s = ctx->mem.alloc(nullptr, ws->bytes);
@@ -349,8 +492,8 @@ bc_status cta_run(Ctx *ctx, Graph *g, CtaWS **wsp, const PlainArgs &a, cudaStrea
   const DeviceGraph *dg = a.g;
   const int n = dg->n;
   const bool sssp = a.out_depth != nullptr;
-  if (a.nsrc <= 0) return BC_OK;
-  bc_status s = cta_ensure(ctx, wsp, n);
+  if (a.nsrc <= 0 && a.ntri <= 0) return BC_OK;
+  bc_status s = cta_ensure(ctx, wsp, n, a.ntri > 0);
   if (s) return s;
   CtaWS *ws = *wsp;
   (void)g;
@@ -371,7 +514,9 @@ bc_status cta_run(Ctx *ctx, Graph *g, CtaWS **wsp, const PlainArgs &a, cudaStrea
   p.out_depth = a.out_depth;
   p.out_sigma = a.out_sigma;
   p.out_ovf = a.out_ovf;
-  const int ncta = std::min(ws->ncta, p.nsrc);
+  p.tri = a.tri;
+  p.ntri = sssp ? 0 : a.ntri;
+  const int ncta = std::max(1, std::min(ws->ncta, std::max(p.nsrc, p.ntri)));
   BC_CUDA_TRY(cudaMemsetAsync(ws->stats, 0, 64, st));
   cudaEvent_t e0, e1;
   BC_CUDA_TRY(cudaEventCreate(&e0));
@@ -400,7 +545,7 @@ bc_status cta_run(Ctx *ctx, Graph *g, CtaWS **wsp, const PlainArgs &a, cudaStrea
   BC_CUDA_TRY(cudaStreamSynchronize(st));
   if (acc) {
     acc->seconds += ms * 1e-3;
-    acc->sources += p.nsrc;
+    acc->sources += p.nsrc + 3ll * p.ntri;
     acc->sigma_overflow_sources += (int64_t)hs[4];
     acc->reached_vertices += (int64_t)hs[0];
     acc->reached_arcs += (int64_t)hs[1];

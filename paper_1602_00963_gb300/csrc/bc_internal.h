@@ -149,6 +149,10 @@ struct PlainArgs {
   uint8_t *out_ovf;
   float alpha;
   float beta;
+  // per-source path on small graphs only: 2-degree triples (a, b, c) run as one unit,
+  // c's DAG derived from those of a and b (device, 3 ints each)
+  const int32_t *tri;
+  int32_t ntri;
 };
 bc_status plain_ensure(Ctx *ctx, PlainWS *ws, int32_t n);
 void plain_free(Ctx *ctx, PlainWS *ws);

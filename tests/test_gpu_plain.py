@@ -185,3 +185,34 @@ def test_wait_limit_timeout_then_recovery(ctx):
     got, _ = bc.bc_exact(h, g.n, PLAIN | bc.BC_PLAIN_GRID)
     assert_bc_close(got, oracle.bc_exact(g), what="after timeout")
     bc.bc_destroy(h)
+
+
+DEG2_GRAPHS = [
+    gg.cycle_graph(101),
+    gg.from_edge_list(6, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 5)]),
+    gg.subdivide_edges(gg.grid2d(30, 30, seed=1, delete_frac=0.1), 0.5, 2),
+    gg.subdivide_edges(gg.grid2d(70, 70), 0.05, 7),  # counts past 2^64 (extended range)
+    gg.subdivide_edges(gg.rmat(10, 4, 5), 0.3, 6),   # with isolated vertices and hubs
+]
+
+
+@pytest.mark.parametrize("gi", range(len(DEG2_GRAPHS)))
+def test_deg2_heuristic_equals_plain(ctx, gi):
+    """BC_DEG2 (Sec. 3.4.2): degree-2 vertices' runs derived from their neighbours' trees
+    give the plain result."""
+    g = DEG2_GRAPHS[gi]
+    h = upload(ctx, g)
+    got, st = bc.bc_exact(h, g.n, PLAIN | bc.BC_DEG2)
+    assert_bc_close(got, oracle.bc_exact(g, nthreads=8), what=f"{g.name} deg2")
+    assert st["sources"] == int((g.degrees() > 0).sum())
+    bc.bc_destroy(h)
+
+
+def test_deg2_flag_rules(ctx):
+    g = gg.cycle_graph(12)
+    h = upload(ctx, g)
+    for bad in (bc.BC_PRUNE_DEG1, bc.BC_PATH_TILED, bc.BC_PLAIN_GRID):
+        with pytest.raises(bc.BCError) as e:
+            bc.bc_exact(h, g.n, PLAIN | bc.BC_DEG2 | bad)
+        assert e.value.status == bc.BC_EINVAL
+    bc.bc_destroy(h)
