@@ -279,6 +279,9 @@ def serving_bench(bc, ctx, rates=(0.5, 1.0, 2.0, 4.0, 8.0), window_s=8.0, seed=1
     Reports p50 / p99 of the latency (submit -> result) and the delivered GTEPS."""
     pool = serving_pool()
     handles = [bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0) for _, g in pool]
+    for (_, g), h in zip(pool, handles):  # kernel choice per graph (not timed)
+        if g.n > 65536:
+            bc.bc_autotune(h, 64, 7)
     nonisolated = [np.flatnonzero(g.degrees() > 0).astype(np.int32) for _, g in pool]
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
@@ -347,14 +350,17 @@ def ba_pruning_bench(bc, ctx):
 def grid_loop_bench(bc, ctx, T: int = 64):
     """2-D 1024 x 1024 grid, 10% of its edges deleted (seed 5), largest component; 1024
     sources uniform from it (seed 6), tiles of T: the level loop as one persistent
-    cooperative kernel, as one launch per phase, and as CUDA-graph chunks of launches."""
+    cooperative kernel, as one launch per phase, and as CUDA-graph chunks of launches; and
+    the per-source path with one source per CTA (the autotuner's choice on this graph)."""
     g = gg.cached("grid", gg.grid2d, 1024, 1024, 5, 0.1)
     src = gg.sample_sources(g, 1024, seed=6)
     h = bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0)
     out = {"n": g.n, "m": g.m, "sources": int(src.size), "tile_width": T}
-    modes = {"persistent": 0, "per_level_launches": bc.BC_LOOP_LAUNCH, "cuda_graph": bc.BC_LOOP_GRAPH}
-    for name, m in modes.items():
-        flags = bc.BC_PATH_TILED | bc.BC_TILE(T) | m
+    modes = {"persistent": bc.BC_PATH_TILED | bc.BC_TILE(T),
+             "per_level_launches": bc.BC_PATH_TILED | bc.BC_TILE(T) | bc.BC_LOOP_LAUNCH,
+             "cuda_graph": bc.BC_PATH_TILED | bc.BC_TILE(T) | bc.BC_LOOP_GRAPH,
+             "per_source_one_per_cta": bc.BC_PATH_PLAIN | bc.BC_PLAIN_CTA}
+    for name, flags in modes.items():
         bc.bc_sources(h, g.n, src[:T], flags)
         _, st = bc.bc_sources(h, g.n, src, flags)
         out[name] = {"gteps": st["gteps"], "seconds": st["seconds"], "levels": st["levels"],

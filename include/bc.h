@@ -58,9 +58,12 @@ enum {
 #define BC_LOOP_LAUNCH    (1u << 5)  /* tile path: one kernel launch per level phase    */
 #define BC_LOOP_GRAPH     (1u << 6)  /* tile path: level loop replayed as a CUDA graph  */
 #define BC_PLAIN_GRID     (1u << 7)  /* per-source path: always the grid-wide kernel     */
+#define BC_PLAIN_CTA      (1u << 13) /* per-source path: one source per CTA at any size  */
 /* (by default the per-source path runs graphs of up to 65,536 vertices one source per CTA,
  *  all SMs on different sources; larger graphs use the grid-wide kernel, one source at a
- *  time over the whole GPU) */
+ *  time over the whole GPU, unless BC_PLAIN_CTA or the autotuner picks the per-CTA kernel,
+ *  which suits sparse high-diameter graphs; it holds 48 bytes per vertex per CTA, two CTAs
+ *  per SM, for graphs of up to 2^24 vertices) */
 /* bc_exact: 2-degree heuristic (Sec. 3.4.2).  A set of degree-2 vertices c, no two sharing
  * a neighbour or being one, is run without a traversal of its own: the shortest-path DAG of c
  * is derived from those of its two neighbours a, b (run from the same CTA) and c's
@@ -141,6 +144,8 @@ typedef struct {
   float alpha;            /* top-down -> bottom-up when frontier arcs > alpha * unvisited arcs */
   float beta;             /* bottom-up -> top-down when frontier vertices < n / beta  */
   int32_t loop_mode;      /* 0 persistent kernel, 1 per-level launches, 2 CUDA graph  */
+  int32_t plain_cta;      /* tile_width 0: 1 = the per-source path runs one source per
+                             CTA at any size (as BC_PLAIN_CTA)                        */
   double probe_seconds;   /* time the tuner spent                                      */
 } bc_tune_result;
 

@@ -19,7 +19,7 @@ __all__ = [
     "bc_stream_submit", "bc_stream_poll", "bc_stream_cancel", "bc_destroy", "bc_sample_sources", "bc_sources_noalloc",
     "bc_set_wait_limit_ms", "BC_OK", "BC_EINVAL", "BC_ENOMEM", "BC_EAGAIN", "BC_ETIMEDOUT",
     "BC_ECUDA", "BC_ENOTFOUND", "BC_ECANCELED", "BC_DEVICE_PTRS", "BC_VALIDATE",
-    "BC_PRUNE_DEG1", "BC_PATH_PLAIN", "BC_PATH_TILED", "BC_LOOP_LAUNCH", "BC_LOOP_GRAPH", "BC_PLAIN_GRID", "BC_DEG2",
+    "BC_PRUNE_DEG1", "BC_PATH_PLAIN", "BC_PATH_TILED", "BC_LOOP_LAUNCH", "BC_LOOP_GRAPH", "BC_PLAIN_GRID", "BC_DEG2", "BC_PLAIN_CTA",
     "BC_TILE", "BC_REQ_EXACT_LIST", "BC_REQ_SAMPLED", "LIB_PATH",
 ]
 
@@ -35,6 +35,7 @@ BC_LOOP_LAUNCH = 1 << 5
 BC_LOOP_GRAPH = 1 << 6
 BC_PLAIN_GRID = 1 << 7
 BC_DEG2 = 1 << 12
+BC_PLAIN_CTA = 1 << 13
 BC_REQ_EXACT_LIST, BC_REQ_SAMPLED = 0, 1
 _STATUS = {0: "BC_OK", 1: "BC_EINVAL", 2: "BC_ENOMEM", 3: "BC_EAGAIN", 4: "BC_ETIMEDOUT",
            5: "BC_ECUDA", 6: "BC_ENOTFOUND", 7: "BC_ECANCELED"}
@@ -64,7 +65,7 @@ class bc_stats(ctypes.Structure):
 
 class bc_tune_result(ctypes.Structure):
     _fields_ = [("tile_width", ctypes.c_int32), ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
-                ("loop_mode", ctypes.c_int32), ("probe_seconds", ctypes.c_double)]
+                ("loop_mode", ctypes.c_int32), ("plain_cta", ctypes.c_int32), ("probe_seconds", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

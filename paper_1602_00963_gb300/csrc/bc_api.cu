@@ -217,7 +217,9 @@ bc_status run_sources(Graph *g, const int32_t *d_src, int32_t k, uint32_t flags,
   pa.max_degree = g->max_degree;
   pa.alpha = alpha;
   pa.beta = beta;
-  if (cta_fits(dg->n) && !(flags & BC_PLAIN_GRID)) return cta_run(ctx, g, &g->cta, pa, st, stats);
+  const bool want_cta = (flags & BC_PLAIN_CTA) || (!(flags & BC_PATH_PLAIN) && g->tune.ready && g->tune.res.plain_cta);
+  if (!(flags & BC_PLAIN_GRID) && (cta_fits(dg->n) || (want_cta && dg->n <= kCtaForcedMaxN)))
+    return cta_run(ctx, g, &g->cta, pa, st, stats);
   bc_status s = plain_ensure(ctx, &g->plain, dg->n);
   if (s) return s;
   return plain_run(ctx, &g->plain, pa, st, stats);
@@ -517,7 +519,8 @@ bc_status bc_sssp(bc_graph *graph, int32_t s, uint32_t flags, int32_t *depth, ui
   std::lock_guard<std::mutex> lk(g->mu);
   cudaStream_t st = c->own_stream;
   const size_t n = (size_t)g->g.n;
-  const bool cta = cta_fits(g->g.n) && !(flags & BC_PLAIN_GRID);
+  const bool cta = !(flags & BC_PLAIN_GRID) &&
+                   (cta_fits(g->g.n) || ((flags & BC_PLAIN_CTA) && g->g.n <= kCtaForcedMaxN));
   bc_status r = cta ? BC_OK : plain_ensure(c, &g->plain, g->g.n);
   if (r) return r;
   // one scratch block carved at 16-byte aligned offsets: sigma | depth | ovf | src

@@ -22,6 +22,7 @@
 // deterministic.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "bc_ff.cuh"
 #include "bc_internal.h"
@@ -93,10 +94,39 @@ __device__ __forceinline__ CtaState cta_carve(char *blk, char *extra, int n) {
   return S;
 }
 
+constexpr int kCtaLaneDeg = 32;  // vertices of degree <= this are handled by one thread
+constexpr int kCtaBig = 512;     // higher-degree vertices listed per pass for whole warps
+
 struct CtaShared {
-  int q, ovf, lovf[2];
+  int q, ovf, lovf[2], nbig;
   unsigned long long ns;
+  int big[kCtaBig];
 };
+
+// Entries Q[i0, i1): a vertex of degree <= kCtaLaneDeg is handled by one thread (a level of
+// a sparse, high-diameter graph then keeps every thread busy), a larger one by a whole warp
+// (lanes over its edges) from a shared list; when the list is full the thread handles it.
+template <typename LaneF, typename WarpF>
+__device__ __forceinline__ void cta_split(const CtaK &p, const int32_t *Q, int i0, int i1, CtaShared &sh,
+                                          LaneF &&lane_f, WarpF &&warp_f) {
+  for (int i = i0 + (int)threadIdx.x; i < i1; i += kCtaThreads) {
+    const int v = Q[i];
+    if (p.rp[v + 1] - p.rp[v] > kCtaLaneDeg) {
+      const int j = atomicAdd(&sh.nbig, 1);
+      if (j < kCtaBig) {
+        sh.big[j] = v;
+        continue;
+      }
+    }
+    lane_f(v);
+  }
+  __syncthreads();
+  const int nb = sh.nbig < kCtaBig ? sh.nbig : kCtaBig;
+  __syncthreads();
+  if (threadIdx.x == 0) sh.nbig = 0;
+  for (int j = (int)(threadIdx.x >> 5); j < nb; j += kCtaWarps) warp_f(sh.big[j]);
+  __syncthreads();
+}
 
 // sigma of v as m 2^e with m in [0.5, 1)
 __device__ __forceinline__ XS cta_sigma(const CtaState &S, int v) {
@@ -139,36 +169,44 @@ __device__ int cta_forward(const CtaK &p, const CtaState &S, int s, CtaShared &s
   __syncthreads();
   int level = 1, q0 = 0, q1 = 1;
   while (q1 > q0) {
-    for (int i = q0 + wid; i < q1; i += kCtaWarps) {
-      const int v = S.Q[i];
-      const unsigned long long sv = S.sig[v];
-      const bool ov = (S.ovf[v >> 5] >> (v & 31)) & 1u;
-      const int e0 = p.rp[v], e1 = p.rp[v + 1];
-      if (lane == 0) *arcs += (unsigned long long)(e1 - e0);
-      for (int e = e0 + lane; e < e1; e += 32) {
-        const int w = p.ci[e];
-        int dw = *(volatile int32_t *)&S.d[w];
-        if (dw < 0) {
-          const int old = atomicCAS(&S.d[w], -1, level);
-          if (old < 0) {
-            S.Q[atomicAdd(&sh.q, 1)] = w;
-            if (p.leaf_term && p.omega) atomicAdd(&sh.ns, 1ull + (unsigned long long)p.omega[w]);
-            dw = level;
-          } else {
-            dw = old;
-          }
-        }
-        if (dw == level) {
-          const unsigned long long old = atomicAdd(&S.sig[w], sv);
-          if (old + sv < old || ov) {
-            atomicOr(&S.ovf[w >> 5], 1u << (w & 31));
-            sh.ovf = 1;
-            sh.lovf[level & 1] = 1;
-          }
+    // discover w from v (the compare-and-swap returns the previous depth) and add sigma
+    auto edge = [&](int w, unsigned long long sv, bool ov) {
+      int dw = *(volatile int32_t *)&S.d[w];
+      if (dw < 0) {
+        const int old = atomicCAS(&S.d[w], -1, level);
+        if (old < 0) {
+          S.Q[atomicAdd(&sh.q, 1)] = w;
+          if (p.leaf_term && p.omega) atomicAdd(&sh.ns, 1ull + (unsigned long long)p.omega[w]);
+          dw = level;
+        } else {
+          dw = old;
         }
       }
-    }
-    __syncthreads();
+      if (dw == level) {
+        const unsigned long long old = atomicAdd(&S.sig[w], sv);
+        if (old + sv < old || ov) {
+          atomicOr(&S.ovf[w >> 5], 1u << (w & 31));
+          sh.ovf = 1;
+          sh.lovf[level & 1] = 1;
+        }
+      }
+    };
+    cta_split(
+        p, S.Q, q0, q1, sh,
+        [&](int v) {
+          const unsigned long long sv = S.sig[v];
+          const bool ov = (S.ovf[v >> 5] >> (v & 31)) & 1u;
+          const int e0 = p.rp[v], e1 = p.rp[v + 1];
+          *arcs += (unsigned long long)(e1 - e0);
+          for (int e = e0; e < e1; e++) edge(p.ci[e], sv, ov);
+        },
+        [&](int v) {
+          const unsigned long long sv = S.sig[v];
+          const bool ov = (S.ovf[v >> 5] >> (v & 31)) & 1u;
+          const int e0 = p.rp[v], e1 = p.rp[v + 1];
+          if (lane == 0) *arcs += (unsigned long long)(e1 - e0);
+          for (int e = e0 + lane; e < e1; e += 32) edge(p.ci[e], sv, ov);
+        });
     const int q2 = sh.q;
     const bool lovf = sh.lovf[level & 1] != 0;
     if (tid == 0) sh.lovf[(level + 1) & 1] = 0;
@@ -176,32 +214,46 @@ __device__ int cta_forward(const CtaK &p, const CtaState &S, int s, CtaShared &s
     if (tid == 0) S.loff[level + 1] = q2;
     if (lovf) {
       // extended-range sigma of the overflowed vertices of this level: the sum over the
-      // parents (level - 1), lanes in edge order, then a fixed-order warp reduction
-      for (int i = q1 + wid; i < q2; i += kCtaWarps) {
-        const int w = S.Q[i];
-        if (!((S.ovf[w >> 5] >> (w & 31)) & 1u)) continue;
-        XS acc;
-        acc.m = 0.0;
-        acc.e = 0;
-        const int e1 = p.rp[w + 1];
-        for (int e = p.rp[w] + lane; e < e1; e += 32) {
-          const int v = p.ci[e];
-          if (S.d[v] == level - 1) xs_add(acc, cta_sigma(S, v));
-        }
+      // parents (level - 1) in edge order (warps: lanes in edge order, then a fixed-order
+      // reduction)
+      cta_split(
+          p, S.Q, q1, q2, sh,
+          [&](int w) {
+            if (!((S.ovf[w >> 5] >> (w & 31)) & 1u)) return;
+            XS acc;
+            acc.m = 0.0;
+            acc.e = 0;
+            for (int e = p.rp[w]; e < p.rp[w + 1]; e++) {
+              const int v = p.ci[e];
+              if (S.d[v] == level - 1) xs_add(acc, cta_sigma(S, v));
+            }
+            acc = xs_norm(acc);
+            S.xm[w] = acc.m;
+            S.xe[w] = acc.e;
+          },
+          [&](int w) {
+            if (!((S.ovf[w >> 5] >> (w & 31)) & 1u)) return;
+            XS acc;
+            acc.m = 0.0;
+            acc.e = 0;
+            const int e1 = p.rp[w + 1];
+            for (int e = p.rp[w] + lane; e < e1; e += 32) {
+              const int v = p.ci[e];
+              if (S.d[v] == level - 1) xs_add(acc, cta_sigma(S, v));
+            }
 #pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-          XS o;
-          o.m = __shfl_down_sync(BC_FULL, acc.m, off);
-          o.e = __shfl_down_sync(BC_FULL, acc.e, off);
-          xs_add(acc, o);
-        }
-        if (lane == 0) {
-          acc = xs_norm(acc);
-          S.xm[w] = acc.m;
-          S.xe[w] = acc.e;
-        }
-      }
-      __syncthreads();
+            for (int off = 16; off >= 1; off >>= 1) {
+              XS o;
+              o.m = __shfl_down_sync(BC_FULL, acc.m, off);
+              o.e = __shfl_down_sync(BC_FULL, acc.e, off);
+              xs_add(acc, o);
+            }
+            if (lane == 0) {
+              acc = xs_norm(acc);
+              S.xm[w] = acc.m;
+              S.xe[w] = acc.e;
+            }
+          });
     }
     q0 = q1;
     q1 = q2;
@@ -213,36 +265,46 @@ __device__ int cta_forward(const CtaK &p, const CtaState &S, int s, CtaShared &s
 
 // Backward sweep of s (Alg. 4 / Alg. 5): sigma of w taken as m 2^e, r stored scaled by 2^e.
 __device__ void cta_backward(const CtaK &p, const CtaState &S, int s, int lmax, double *bcp,
-                             const CtaShared &sh) {
+                             CtaShared &sh) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const float2 wsrc = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[s] : 0ull));
   for (int dd = lmax; dd >= 1; --dd) {
-    const int a0 = S.loff[dd], a1 = S.loff[dd + 1];
-    for (int i = a0 + wid; i < a1; i += kCtaWarps) {
-      const int w = S.Q[i];
-      const XS sw = cta_sigma(S, w);
-      float2 acc = make_float2(0.0f, 0.0f);
-      if (dd < lmax) {
-        const int e1 = p.rp[w + 1];
-        for (int e = p.rp[w] + lane; e < e1; e += 32) {
-          const int v = p.ci[e];
-          if (S.d[v] != dd + 1) continue;
-          ff_add(acc, ff_scale(S.r[v], sw.e - cta_exp(S, v)));
-        }
+    // commit of w from the sum of its successors' r (rescaled to w's exponent)
+    auto commit = [&](int w, const XS &sw, float2 acc) {
+      const float2 mw = ff_mant(sw.m);
+      const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
+      float2 rw = ff_mul(om1, ff_rcp(mw));
+      ff_add(rw, acc);
+      S.r[w] = rw;  // r scaled by 2^e of w
+      const float2 dl = ff_mul(wsrc, ff_mul(mw, acc));
+      if (!ff_zero(dl)) bcp[w] += ff_to(dl);
+    };
+    cta_split(
+        p, S.Q, S.loff[dd], S.loff[dd + 1], sh,
+        [&](int w) {
+          const XS sw = cta_sigma(S, w);
+          float2 acc = make_float2(0.0f, 0.0f);
+          if (dd < lmax)
+            for (int e = p.rp[w]; e < p.rp[w + 1]; e++) {
+              const int v = p.ci[e];
+              if (S.d[v] == dd + 1) ff_add(acc, ff_scale(S.r[v], sw.e - cta_exp(S, v)));
+            }
+          commit(w, sw, acc);
+        },
+        [&](int w) {
+          const XS sw = cta_sigma(S, w);
+          float2 acc = make_float2(0.0f, 0.0f);
+          if (dd < lmax) {
+            const int e1 = p.rp[w + 1];
+            for (int e = p.rp[w] + lane; e < e1; e += 32) {
+              const int v = p.ci[e];
+              if (S.d[v] == dd + 1) ff_add(acc, ff_scale(S.r[v], sw.e - cta_exp(S, v)));
+            }
 #pragma unroll
-        for (int m = 16; m >= 1; m >>= 1) ff_add(acc, ff_shfl_xor(acc, m));
-      }
-      if (lane == 0) {
-        const float2 mw = ff_mant(sw.m);
-        const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
-        float2 rw = ff_mul(om1, ff_rcp(mw));
-        ff_add(rw, acc);
-        S.r[w] = rw;  // r scaled by 2^e of w
-        const float2 dl = ff_mul(wsrc, ff_mul(mw, acc));
-        if (!ff_zero(dl)) bcp[w] += ff_to(dl);
-      }
-    }
-    __syncthreads();
+            for (int m = 16; m >= 1; m >>= 1) ff_add(acc, ff_shfl_xor(acc, m));
+          }
+          if (lane == 0) commit(w, sw, acc);
+        });
   }
   if (tid == 0 && p.leaf_term && p.omega && p.omega[s] > 0) {
     const double om = (double)p.omega[s];
@@ -350,6 +412,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_cta_sources(CtaK p) {
   __shared__ CtaShared sh;
 
   for (int v = tid; v < n; v += kCtaThreads) bcp[v] = 0.0;
+  if (tid == 0) sh.nbig = 0;  // the big-vertex list of cta_split starts empty
   cta_clear(A, n);
   if (p.ntri) cta_clear(B, n);
   unsigned long long my_arcs = 0, my_reached = 0, my_levels = 0, my_deep = 0, my_ovf = 0;
@@ -437,8 +500,20 @@ static bc_status cta_ensure(Ctx *ctx, CtaWS **wsp, int n, bool tri) {
   const int in_smem = st <= kCtaSmemMax;
   const size_t smem = in_smem ? st : 0;
   int bps = 0;
-  if (smem > 48 * 1024) {
-    BC_CUDA_TRY(cudaFuncSetAttribute(k_cta_sources, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    // the attribute is per function and device: set it once, to the largest size used, so
+    // that concurrent callers (serving workers on graphs of different sizes) never lower it
+    // under another's launch
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    BC_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+      BC_CUDA_TRY(cudaFuncSetAttribute(k_cta_sources, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kCtaSmemMax));
+      if (dev >= 0 && dev < 64) done[dev] = true;
+    }
   }
   BC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_cta_sources, kCtaThreads, smem));
   if (bps < 1) return fail(BC_ECUDA, "CTA per-source kernel does not fit on an SM");

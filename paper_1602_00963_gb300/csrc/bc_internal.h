@@ -161,7 +161,8 @@ bc_status plain_run_view(const PlainWS &ws, const PlainArgs &a, int num_sms, uin
                          cudaStream_t st, int *dev_err);
 
 // ---- per-source path on small graphs: one CTA per source (bc_cta.cu)
-constexpr int32_t kCtaMaxN = 65536;
+constexpr int32_t kCtaMaxN = 65536;        // default for the per-source path up to this size
+constexpr int32_t kCtaForcedMaxN = 1 << 24;  // BC_PLAIN_CTA / tuned: up to this size
 bool cta_fits(int32_t n);
 // Runs a.src, one source per CTA (a.out_depth set: forward only for a.src[0], depth / sigma /
 // overflow exported).

@@ -11,9 +11,9 @@
 //     dependencies are routed to its own request's accumulator);
 //   * run the tile with per-phase launches (not the cooperative kernel) so that tiles of
 //     different graphs, on different streams, overlap on the device;
-//   * on small graphs (up to 65,536 vertices) instead run one request's remaining sources
-//     on the per-source CTA kernel (each CTA a source at a time, all SMs busy), which
-//     there is far faster than a tile;
+//   * on small graphs (up to 65,536 vertices), and on graphs the autotuner gave to it,
+//     instead run one request's remaining sources on the per-source CTA kernel (each CTA a
+//     source at a time, all SMs busy), which there is far faster than a tile;
 //   * complete a request when its last tile is done: copy its BC to the caller's buffer.
 // A request that arrives while others run is admitted as soon as memory allows and its
 // sources join the next tiles of its graph.
@@ -92,7 +92,8 @@ int tile_width_for(Graph *g) {
 
 size_t tile_ws_estimate(Graph *g, int T) {
   const size_t n = (size_t)g->g.n, G = (size_t)T / 32;
-  if (cta_fits(g->g.n)) return n * 64;  // CTA kernel: it shrinks its partials to the budget
+  if (cta_fits(g->g.n) || (g->tune.ready && g->tune.res.tile_width == 0 && g->tune.res.plain_cta))
+    return n * 64;  // CTA kernel: it shrinks its partials to the budget
   return n * G * 20 + n * T * 16 + n * (20 + 12 * G) * 4;
 }
 
@@ -196,8 +197,10 @@ void worker_main(Server *sv, int wid) {
       continue;
     }
     Graph *g = job->g;
-    if (cta_fits(g->g.n)) {
-      // small graph: the remaining sources of its first unscheduled request, one launch
+    if (cta_fits(g->g.n) || (g->tune.ready && g->tune.res.tile_width == 0 && g->tune.res.plain_cta &&
+                             g->g.n <= kCtaForcedMaxN)) {
+      // small graph (or one the autotuner gave to the per-CTA kernel): the remaining sources
+      // of its first unscheduled request, one launch
       Req *r = nullptr;
       for (Req *q : sv->active)
         if (q->g == g && !q->canceled && q->next < q->src.size()) {

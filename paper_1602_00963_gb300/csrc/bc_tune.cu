@@ -77,18 +77,24 @@ bc_status time_config(const Probe &pr, int T, float alpha, int loop_mode, double
   for (int rep = 0; rep < 2; rep++) {
     bc_stats s{};
     bc_status r;
-    if (T == 0) {
-      r = plain_ensure(pr.g->ctx, &pr.g->plain, pr.g->g.n);
-      if (r) return r;
+    if (T <= 0) {  // per-source path: 0 = the kernel chosen by size, -1 = one source per CTA
+      const bool cta = T < 0 || cta_fits(pr.g->g.n);
       PlainArgs pa{};
       pa.g = &pr.g->g;
       pa.src = pr.d_src;
-      pa.nsrc = pr.k < 32 ? pr.k : 32;  // the per-source path is timed on fewer sources
+      // the grid-wide kernel is timed on fewer sources; the per-CTA kernel needs enough
+      // sources to fill the GPU
+      pa.nsrc = cta ? pr.k : (pr.k < 32 ? pr.k : 32);
       pa.bc = pr.d_bc;
       pa.max_degree = pr.g->max_degree;
       pa.alpha = alpha;
       pa.beta = 24.f;
-      r = plain_run(pr.g->ctx, &pr.g->plain, pa, pr.st, &s);
+      if (cta) {
+        r = cta_run(pr.g->ctx, pr.g, &pr.g->cta, pa, pr.st, &s);
+      } else {
+        r = plain_ensure(pr.g->ctx, &pr.g->plain, pr.g->g.n);
+        if (!r) r = plain_run(pr.g->ctx, &pr.g->plain, pa, pr.st, &s);
+      }
     } else {
       TileArgs ta{};
       ta.g = &pr.g->g;
@@ -140,6 +146,7 @@ bool cache_lookup(const std::string &key, bc_tune_result *res) {
     if ((p = strstr(line, "\"alpha\": "))) r.alpha = (float)atof(p + 9);
     if ((p = strstr(line, "\"beta\": "))) r.beta = (float)atof(p + 8);
     if ((p = strstr(line, "\"loop_mode\": "))) r.loop_mode = atoi(p + 13);
+    if ((p = strstr(line, "\"plain_cta\": "))) r.plain_cta = atoi(p + 13);
     *res = r;
     found = true;  // the last matching line wins
   }
@@ -151,8 +158,8 @@ void cache_store(const std::string &key, const bc_tune_result &r) {
   const char *path = getenv("BC_TUNE_CACHE");
   if (!path) return;
   if (FILE *f = fopen(path, "a")) {
-    fprintf(f, "{\"key\": \"%s\", \"tile_width\": %d, \"alpha\": %.4f, \"beta\": %.2f, \"loop_mode\": %d, \"probe_seconds\": %.3f}\n",
-            key.c_str(), r.tile_width, r.alpha, r.beta, r.loop_mode, r.probe_seconds);
+    fprintf(f, "{\"key\": \"%s\", \"tile_width\": %d, \"alpha\": %.4f, \"beta\": %.2f, \"loop_mode\": %d, \"plain_cta\": %d, \"probe_seconds\": %.3f}\n",
+            key.c_str(), r.tile_width, r.alpha, r.beta, r.loop_mode, r.plain_cta, r.probe_seconds);
     fclose(f);
   }
 }
@@ -225,16 +232,19 @@ extern "C" bc_status bc_autotune(bc_graph *graph, int32_t probe_sources, uint64_
     s = time_config(pr, bestT, bestA, m, &t);
     if (!s && t < best * 0.97) best = t, bestMode = m;
   }
-  // stage 4: the per-source path
-  double tplain = 1e30;
+  // stage 4: the per-source path (the kernel chosen by size, and on larger graphs also one
+  // source per CTA, which suits sparse high-diameter graphs)
+  double tplain = 1e30, tcta = 1e30;
   if (!s) s = time_config(pr, 0, 0.5f, 0, &tplain);
+  if (!s && !cta_fits(g->g.n) && g->g.n <= kCtaForcedMaxN) s = time_config(pr, -1, 0.5f, 0, &tcta);
   c->mem.release(pr.d_src, hs.size() * 4 + 4);
   c->mem.release(pr.d_bc, (size_t)g->g.n * 8);
   if (s) return s;
-  if (tplain < best) {
+  if (std::min(tplain, tcta) < best) {
     res.tile_width = 0;
     res.alpha = 0.5f;
     res.loop_mode = 0;
+    res.plain_cta = tcta < tplain ? 1 : 0;
   } else {
     res.tile_width = bestT;
     res.alpha = bestA;

@@ -110,3 +110,18 @@ def test_ba262144_pruned_equals_unpruned(ctx):
         d, sg, o = bc.bc_sssp(h, g.n, int(x))
         assert_sssp_equal((d, sg, o), oracle.sssp(g, int(x)), f"ba262144 source {x}")
     bc.bc_destroy(h)
+
+
+def test_grid1024_per_source_cta_vs_oracle(ctx):
+    """The per-CTA per-source kernel on a graph of a million vertices (BC_PLAIN_CTA): 304
+    sources at a time, state in global memory, counts past 2^64 on the extended range."""
+    g = gg.cached("grid", gg.grid2d, 1024, 1024, 5, 0.1)
+    src = gg.sample_sources(g, 1024, seed=6)
+    h = upload(ctx, g)
+    s = src[:48]
+    got, st = bc.bc_sources(h, g.n, s, bc.BC_PATH_PLAIN | bc.BC_PLAIN_CTA)
+    assert st["sigma_overflow_sources"] == s.size
+    assert_bc_close(got, oracle.bc(g, s), what="grid1024 per-source CTA")
+    d, sg, o = bc.bc_sssp(h, g.n, int(s[3]), bc.BC_PLAIN_CTA)
+    assert_sssp_equal((d, sg, o), oracle.sssp(g, int(s[3])), "grid1024 CTA sssp")
+    bc.bc_destroy(h)
