@@ -19,17 +19,21 @@
 // Backward level d (Alg. 5 with updateDep): each entry (w, M_w) of A_d sums r[v] over the
 // neighbours v whose level-(d+1) mask shares bits with M_w; then delta = sigma * sum,
 // BC[w] += sum over lanes of (omega[s]+1) * delta (fixed lane order) and r[w] = (1 +
-// delta + omega[w]) / sigma.
+// omega[w]) / sigma + sum.  r and its sums are float-float pairs (bc_ff.cuh): FP64 is slow
+// on this GPU, and only the per-vertex BC update uses it.
 //
 // Work mapping (active-edge parallelism, Sec. 3.1): every list that is walked (active
 // vertices, candidates, all vertices) carries an exclusive degree prefix, produced by the
-// packed (count, edges) append counter or built once per graph.  A warp takes an equal
-// slice of the concatenated adjacency, snapped to list-entry starts so each entry belongs
-// to one warp, and maps edge -> entry by a search in the prefix.  Lanes are edges for the
-// frontier-mask tests and sources for the sigma / r row gathers of the edges that hit.
-// Vertices of degree >= kHub are skipped by the walk and processed by a whole CTA
-// (shared-memory reduction in warp order).  All sums run in a fixed order, so the tile
-// path is deterministic.
+// packed (count, edges) append counter or built once per graph.  A warp takes ranges of
+// the concatenated adjacency (a static first range, then guided claims), snapped to
+// list-entry starts so each entry belongs to one warp, and maps edge -> entry by a search
+// in the prefix.  Lanes are edges for the frontier-mask tests; a hit of at most two
+// sources is loaded by its own lane, denser hits are gathered as sigma / r rows by the
+// source lanes.  Levels whose entries average at most two sources and 16 edges (high-
+// diameter graphs) run one entry per lane instead.  Vertices of degree >= kHub are
+// processed by whole CTAs (forward) or as 4096-edge items spread over CTAs (backward).
+// Warp-level work is numbered across CTAs first.  All sums run in a fixed order, so the
+// tile path is deterministic.
 //
 // sigma beyond 2^64: a tile first runs with r computed from sigma mod 2^64; if any count
 // overflowed, the tile is rerun (before any BC update) in extended mode, where each
@@ -2138,9 +2142,10 @@ void tile_free(Ctx *ctx, TileWS *ws) {
   delete ws;
 }
 
-#define TA(ptr, bytes)                                                             \
-  do {                                                                             \
-    if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes) ? (bytes) : 16); \
+#define TA(ptr, bytes)                                                                    \
+  do {                                                                                    \
+    const size_t b_ = (bytes);                                                            \
+    if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), b_ != 0 ? b_ : (size_t)16);     \
   } while (0)
 
 static bc_status ws_main(Ctx *ctx, TileWS *ws, int n, int T) {
