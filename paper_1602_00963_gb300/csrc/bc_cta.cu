@@ -21,6 +21,7 @@
 // (omega[s] + 1) * delta.  A second kernel sums the partials in CTA order, so the result is
 // deterministic.
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <mutex>
 
@@ -95,6 +96,8 @@ __device__ __forceinline__ CtaState cta_carve(char *blk, char *extra, int n) {
 }
 
 constexpr int kCtaLaneDeg = 32;  // vertices of degree <= this are handled by one thread
+constexpr int kStage = 4;        // state in global memory: a thread's edges are loaded
+                                 // kStage at a time (their latencies overlap)
 constexpr int kCtaBig = 512;     // higher-degree vertices listed per pass for whole warps
 
 struct CtaShared {
@@ -194,11 +197,47 @@ __device__ int cta_forward(const CtaK &p, const CtaState &S, int s, CtaShared &s
     cta_split(
         p, S.Q, q0, q1, sh,
         [&](int v) {
+          // one thread: the edges in groups of kStage, each stage's loads and atomics of
+          // the group in flight together
           const unsigned long long sv = S.sig[v];
           const bool ov = (S.ovf[v >> 5] >> (v & 31)) & 1u;
           const int e0 = p.rp[v], e1 = p.rp[v + 1];
           *arcs += (unsigned long long)(e1 - e0);
-          for (int e = e0; e < e1; e++) edge(p.ci[e], sv, ov);
+          if (p.in_smem) {  // state in shared memory: loads are cheap, no staging
+            for (int e = e0; e < e1; e++) edge(p.ci[e], sv, ov);
+            return;
+          }
+          for (int e = e0; e < e1; e += kStage) {
+            int w[kStage], dw[kStage];
+#pragma unroll
+            for (int j = 0; j < kStage; j++) w[j] = e + j < e1 ? p.ci[e + j] : -1;
+#pragma unroll
+            for (int j = 0; j < kStage; j++) dw[j] = w[j] >= 0 ? *(volatile int32_t *)&S.d[w[j]] : INT_MAX;
+#pragma unroll
+            for (int j = 0; j < kStage; j++) {
+              if (w[j] < 0 || dw[j] >= 0) continue;
+              const int old = atomicCAS(&S.d[w[j]], -1, level);
+              if (old < 0) {
+                S.Q[atomicAdd(&sh.q, 1)] = w[j];
+                if (p.leaf_term && p.omega) atomicAdd(&sh.ns, 1ull + (unsigned long long)p.omega[w[j]]);
+                dw[j] = level;
+              } else {
+                dw[j] = old;
+              }
+            }
+            unsigned long long old[kStage];
+#pragma unroll
+            for (int j = 0; j < kStage; j++) old[j] = (w[j] >= 0 && dw[j] == level) ? atomicAdd(&S.sig[w[j]], sv) : 0ull;
+#pragma unroll
+            for (int j = 0; j < kStage; j++) {
+              if (w[j] < 0 || dw[j] != level) continue;
+              if (old[j] + sv < old[j] || ov) {
+                atomicOr(&S.ovf[w[j] >> 5], 1u << (w[j] & 31));
+                sh.ovf = 1;
+                sh.lovf[level & 1] = 1;
+              }
+            }
+          }
         },
         [&](int v) {
           const unsigned long long sv = S.sig[v];
@@ -223,9 +262,25 @@ __device__ int cta_forward(const CtaK &p, const CtaState &S, int s, CtaShared &s
             XS acc;
             acc.m = 0.0;
             acc.e = 0;
-            for (int e = p.rp[w]; e < p.rp[w + 1]; e++) {
+            const int e1 = p.rp[w + 1];
+            for (int e = p.rp[w]; e < e1 && p.in_smem; e++) {
               const int v = p.ci[e];
               if (S.d[v] == level - 1) xs_add(acc, cta_sigma(S, v));
+            }
+            for (int e = p.rp[w]; e < e1 && !p.in_smem; e += kStage) {
+              int v[kStage];
+              bool par[kStage];
+              XS x[kStage];
+#pragma unroll
+              for (int j = 0; j < kStage; j++) v[j] = e + j < e1 ? p.ci[e + j] : -1;
+#pragma unroll
+              for (int j = 0; j < kStage; j++) par[j] = v[j] >= 0 && S.d[v[j]] == level - 1;
+#pragma unroll
+              for (int j = 0; j < kStage; j++)
+                if (par[j]) x[j] = cta_sigma(S, v[j]);
+#pragma unroll
+              for (int j = 0; j < kStage; j++)
+                if (par[j]) xs_add(acc, x[j]);
             }
             acc = xs_norm(acc);
             S.xm[w] = acc.m;
@@ -284,11 +339,32 @@ __device__ void cta_backward(const CtaK &p, const CtaState &S, int s, int lmax, 
         [&](int w) {
           const XS sw = cta_sigma(S, w);
           float2 acc = make_float2(0.0f, 0.0f);
-          if (dd < lmax)
+          if (dd < lmax && p.in_smem) {
             for (int e = p.rp[w]; e < p.rp[w + 1]; e++) {
               const int v = p.ci[e];
               if (S.d[v] == dd + 1) ff_add(acc, ff_scale(S.r[v], sw.e - cta_exp(S, v)));
             }
+          } else if (dd < lmax) {
+            const int e1 = p.rp[w + 1];
+            for (int e = p.rp[w]; e < e1; e += kStage) {
+              int v[kStage];
+              bool suc[kStage];
+              float2 x[kStage];
+              int ev[kStage];
+#pragma unroll
+              for (int j = 0; j < kStage; j++) v[j] = e + j < e1 ? p.ci[e + j] : -1;
+#pragma unroll
+              for (int j = 0; j < kStage; j++) suc[j] = v[j] >= 0 && S.d[v[j]] == dd + 1;
+#pragma unroll
+              for (int j = 0; j < kStage; j++) {
+                x[j] = suc[j] ? S.r[v[j]] : make_float2(0.0f, 0.0f);
+                ev[j] = suc[j] ? cta_exp(S, v[j]) : 0;
+              }
+#pragma unroll
+              for (int j = 0; j < kStage; j++)
+                if (suc[j]) ff_add(acc, ff_scale(x[j], sw.e - ev[j]));
+            }
+          }
           commit(w, sw, acc);
         },
         [&](int w) {
@@ -390,7 +466,7 @@ __device__ void cta_backward_deg2(const CtaK &p, const CtaState &A, const CtaSta
   }
 }
 
-__global__ void __launch_bounds__(kCtaThreads) k_cta_sources(CtaK p) {
+__global__ void __launch_bounds__(kCtaThreads, 2) k_cta_sources(CtaK p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = p.n;
   const int tid = threadIdx.x, lane = tid & 31;
