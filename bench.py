@@ -34,6 +34,7 @@ if ROOT not in sys.path:
 
 import graphgen as gg  # noqa: E402
 
+METRIC = "BC GTEPS (sources·m/s) batched vs per-source on 1 GB300; serving p50/p99 latency"
 WORKLOAD = {
     "workload": "rmat-s20-ef16 batched exact BC, 4096 LCC sources",
     "graph": "R-MAT scale 20, edge factor 16, a/b/c/d .57/.19/.19/.05, seed 3",
@@ -246,7 +247,7 @@ def run_reference(args, rank, world):
         times.append(time.perf_counter() - t)
     dt = statistics.median(times)
     value = k * g.m / dt / 1e9
-    line = {"metric": "BC GTEPS (sources*m/s)", "value": value, "unit": "GTEPS", "n_gpus": 0,
+    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference", "config": dict(WORKLOAD),
@@ -602,7 +603,7 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "BC GTEPS (sources·m/s) batched vs per-source on 1 GB300; serving p50/p99 latency",
+            "metric": METRIC,
             "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
