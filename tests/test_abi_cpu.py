@@ -51,3 +51,14 @@ def test_algorithmic_bytes_model():
     st = {"reached_vertices": 1000, "reached_arcs": 20000}
     assert bench.algorithmic_bytes(st, 1) == 8 * 20000 + 84 * 1000
     assert bench.algorithmic_bytes(st, 64) == (8 * 20000 + 16 * 1000) / 64 + 68 * 1000
+
+
+def test_bench_deg2_triple_count_matches_the_selection_rule():
+    """bench.py reports the number of derived 2-degree runs with the library's rule; it
+    must agree with the oracle's statement of the same rule."""
+    import bench
+    import graphgen as gg
+    from oracle import deg2
+    for g in [gg.cycle_graph(17), gg.subdivide_edges(gg.grid2d(12, 12, seed=1, delete_frac=0.1), 0.4, 2),
+              gg.random_tree(60, 4)]:
+        assert bench.deg2_triples(g) == len(deg2.select_triples(g))
