@@ -48,6 +48,7 @@ struct CtaK {
   char *gws;          // per-CTA global slices (state when not in shared memory, level offsets)
   size_t slice;       // bytes per slice
   int in_smem;        // state arrays in shared memory
+  int clean;          // state in global memory already cleared (left clean by the last call)
   unsigned long long *stats;  // reached pairs, their arcs, levels, deepest level (max),
                               // sources whose sigma passed 2^64
   const int32_t *tri;         // 2-degree triples (a, b, c), 3 ints each
@@ -489,8 +490,10 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_cta_sources(CtaK p) {
 
   for (int v = tid; v < n; v += kCtaThreads) bcp[v] = 0.0;
   if (tid == 0) sh.nbig = 0;  // the big-vertex list of cta_split starts empty
-  cta_clear(A, n);
-  if (p.ntri) cta_clear(B, n);
+  // every source resets the vertices it reached, so state in global memory stays clean from
+  // one call to the next; shared memory starts undefined
+  if (p.in_smem || !p.clean) cta_clear(A, n);
+  if (p.ntri && !p.clean) cta_clear(B, n);
   unsigned long long my_arcs = 0, my_reached = 0, my_levels = 0, my_deep = 0, my_ovf = 0;
   __syncthreads();
 
@@ -554,6 +557,7 @@ __global__ void k_cta_reduce(const double *bcp, int ncta, int n, double *bc) {
 
 struct CtaWS {
   int n = 0, ncta = 0, in_smem = 0, tri = 0;
+  bool clean = false;  // global-memory state left cleared by a completed launch
   size_t slice = 0, smem = 0;
   double *bcp = nullptr;
   char *gws = nullptr;
@@ -661,6 +665,7 @@ bc_status cta_run(Ctx *ctx, Graph *g, CtaWS **wsp, const PlainArgs &a, cudaStrea
   p.gws = ws->gws;
   p.slice = ws->slice;
   p.in_smem = ws->in_smem;
+  p.clean = ws->clean ? 1 : 0;
   p.stats = ws->stats;
   p.out_depth = a.out_depth;
   p.out_sigma = a.out_sigma;
@@ -673,6 +678,8 @@ bc_status cta_run(Ctx *ctx, Graph *g, CtaWS **wsp, const PlainArgs &a, cudaStrea
   BC_CUDA_TRY(cudaEventCreate(&e0));
   BC_CUDA_TRY(cudaEventCreate(&e1));
   cudaEventRecord(e0, st);
+  const bool was_clean = ws->clean;
+  ws->clean = false;  // until the launch is known to have completed
   k_cta_sources<<<ncta, kCtaThreads, ws->smem, st>>>(p);
   cudaError_t le = cudaGetLastError();
   if (le == cudaSuccess && !sssp && a.bc) {
@@ -694,6 +701,8 @@ bc_status cta_run(Ctx *ctx, Graph *g, CtaWS **wsp, const PlainArgs &a, cudaStrea
   cudaEventDestroy(e1);
   if (se != cudaSuccess) return cuda_fail(se, "CTA per-source kernel");
   BC_CUDA_TRY(cudaStreamSynchronize(st));
+  // the launched CTAs left their state cleared; CTAs not launched kept theirs
+  ws->clean = was_clean || ncta == ws->ncta;
   if (acc) {
     acc->seconds += ms * 1e-3;
     acc->sources += p.nsrc + 3ll * p.ntri;
