@@ -65,7 +65,7 @@ def profile_case(spec: str):
     ('tile:T:K', 'plain:K') or on the 1024 x 1024 deleted-edge grid ('grid:T:K'; its
     sigma needs the extended range, so the tile runs twice when it starts in 64-bit mode),
     or the per-source path on R-MAT scale 12 with its first K non-isolated sources
-    ('small:K', one source per CTA)."""
+    ('small:K', one source per CTA), or one source per CTA on the grid ('gridcta:K')."""
     import paper_1602_00963_gb300 as bc
     parts = spec.split(":")
     if parts[0] == "grid":
@@ -74,6 +74,9 @@ def profile_case(spec: str):
     elif parts[0] == "small":
         g = gg.rmat(12, 16, 1)
         src = np.flatnonzero(g.degrees() > 0).astype(np.int32)
+    elif parts[0] == "gridcta":
+        g = gg.cached("grid", gg.grid2d, 1024, 1024, 5, 0.1)
+        src = gg.sample_sources(g, 1024, seed=6)
     else:
         g, src = load_workload(4096, 0)
     ctx = bc.bc_ctx_create(0)
@@ -83,8 +86,8 @@ def profile_case(spec: str):
         flags = bc.BC_PATH_TILED | bc.BC_TILE(T)
     else:
         k = int(parts[1])
-        flags = bc.BC_PATH_PLAIN
-    if parts[0] == "small":
+        flags = bc.BC_PATH_PLAIN | (bc.BC_PLAIN_CTA if parts[0] == "gridcta" else 0)
+    if parts[0] in ("small", "gridcta"):
         bc.bc_sources(h, g.n, src[:k], flags)  # warm-up: workspace and shared-memory setup
     _, st = bc.bc_sources(h, g.n, src[:k], flags)
     print(json.dumps({"profile_case": spec, "seconds": st["seconds"], "gteps": st["gteps"],
