@@ -79,7 +79,9 @@ def profile_case(spec: str):
         src = gg.sample_sources(g, 1024, seed=6)
     else:
         g, src = load_workload(4096, 0)
-    ctx = bc.bc_ctx_create(0)
+    # gridcta: a 2.5 GB budget keeps the per-CTA workspace (and what a profiler saves
+    # between its passes) small; the kernel then runs fewer CTAs
+    ctx = bc.bc_ctx_create(0, (5 << 29) if parts[0] == "gridcta" else 0)
     h = bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0)
     if parts[0] in ("tile", "grid"):
         T, k = int(parts[1]), int(parts[2])
