@@ -199,6 +199,19 @@ def subdivide_edges(g: Graph, frac: float, seed: int) -> Graph:
     return csr_from_edges(g.n + k, s2, d2, f"{g.name}-sub{frac}-seed{seed}")
 
 
+def attach_leaves(g: Graph, frac: float, seed: int, max_leaves: int = 3) -> Graph:
+    """A seeded fraction of the vertices each gain 1..max_leaves pendant vertices (ids n,
+    n + 1, ... in vertex order): leaf-rich inputs for the 1-degree reduction."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pick = np.flatnonzero(rng.random(g.n) < frac)
+    cnt = rng.integers(1, max_leaves + 1, pick.size)
+    hub = np.repeat(pick, cnt).astype(np.int64)
+    leaf = g.n + np.arange(hub.size, dtype=np.int64)
+    src, dst = g.edges()
+    return csr_from_edges(g.n + hub.size, np.concatenate([src, hub]), np.concatenate([dst, leaf]),
+                          f"{g.name}-leaves{frac}-seed{seed}")
+
+
 # ------------------------------------------------------------------- Erdos-Renyi
 def erdos_renyi(n: int, m: int, seed: int) -> Graph:
     """G(n, M): exactly M distinct undirected edges drawn uniformly."""

@@ -11,6 +11,12 @@ through a or b, so (Lemma 1 of Sec. 3.4.2, Bellman criterion):
 and level_c(c) = 0, sigma_c(c) = 1.  c's dependencies are then accumulated on that DAG
 (Eq. 2) instead of after a traversal from c.  Integers are exact (Python ints) and
 dependencies exact rationals, so this is usable on small graphs only.
+
+Combined with the 1-degree reduction (Sec. 3.4.1, Eq. 3/4, Alg. 6), the triples are chosen
+on the residual graph and every run, derived or not, carries the leaf weights omega: the
+dependency recursion adds omega(v) for each successor v, a run from s counts omega(s) + 1
+times, and s gains omega(s)(2 n_s - omega(s) - 3) with n_s the weighted size of its
+component (the pre-increment reading of Eq. 3).
 """
 from __future__ import annotations
 
@@ -61,16 +67,18 @@ def derive(adj, c, a_tree, b_tree):
     return lvl, sig
 
 
-def dependencies(adj, s, lvl, sig):
-    """delta_s(v) for every v (Eq. 2), processing the DAG given by lvl / sig deepest first."""
+def dependencies(adj, s, lvl, sig, omega=None):
+    """delta_s(v) for every v (Eq. 2; with leaf weights omega, Eq. 4's recursion), processing
+    the DAG given by lvl / sig deepest first."""
     n = len(adj)
+    om = omega if omega is not None else [0] * n
     order = sorted((v for v in range(n) if lvl[v] >= 0), key=lambda v: -lvl[v])
     delta = [Fraction(0)] * n
     for w in order:
         acc = Fraction(0)
         for v in adj[w]:
             if lvl[v] == lvl[w] + 1:
-                acc += Fraction(1) / sig[v] * (1 + delta[v])
+                acc += Fraction(1) / sig[v] * (1 + om[v] + delta[v])
         delta[w] = sig[w] * acc
     delta[s] = Fraction(0)
     return delta
@@ -93,22 +101,33 @@ def select_triples(g):
     return out
 
 
-def bc_with_deg2(g):
+def bc_with_deg2(g, prune: bool = False):
     """Exact BC (ordered pairs) over all sources, each selected degree-2 vertex's run taken
-    from its neighbours' trees; returns (bc as Fractions, number of derived sources)."""
+    from its neighbours' trees; returns (bc as Fractions, number of derived sources).
+    With ``prune`` the 1-degree reduction comes first (one round, as the C oracle's
+    prune_deg1) and both heuristics run on the residual graph."""
+    omega = None
+    if prune:
+        from oracle import prune_deg1
+        om, _, g = prune_deg1(g)
+        omega = [int(x) for x in om]
+    om = omega if omega is not None else [0] * g.n
     adj = _adj(g)
     bc = [Fraction(0)] * g.n
     triples = select_triples(g)
     derived = {c: (a, b) for a, b, c in triples}
     for s in range(g.n):
-        if not adj[s]:
+        if not adj[s] and om[s] == 0:
             continue
         if s in derived:
             a, b = derived[s]
             lvl, sig = derive(adj, s, bfs(adj, a), bfs(adj, b))
         else:
             lvl, sig = bfs(adj, s)
-        d = dependencies(adj, s, lvl, sig)
+        d = dependencies(adj, s, lvl, sig, omega)
         for v in range(g.n):
-            bc[v] += d[v]
+            bc[v] += (om[s] + 1) * d[v]
+        if om[s] > 0:
+            n_s = sum(1 + om[v] for v in range(g.n) if lvl[v] >= 0)
+            bc[s] += om[s] * (2 * n_s - om[s] - 3)
     return bc, len(triples)

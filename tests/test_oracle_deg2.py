@@ -71,3 +71,39 @@ def test_selection_is_disjoint():
     assert len(seen) == len(set(seen)) and len(tri) > 10
     deg = g.degrees()
     assert all(deg[c] == 2 for _, _, c in tri)
+
+
+H3_GRAPHS = [
+    gg.random_tree(40, 5),                                            # residual full of chains
+    gg.attach_leaves(gg.cycle_graph(11), 0.5, 1),
+    gg.attach_leaves(gg.subdivide_edges(gg.grid2d(5, 5, seed=1, delete_frac=0.15), 0.5, 2), 0.3, 3),
+    gg.attach_leaves(gg.subdivide_edges(gg.gnm(30, 45, 4), 0.4, 5), 0.4, 6),
+    gg.from_edge_list(7, [(0, 1), (1, 2), (2, 3), (3, 4), (2, 5), (5, 6)]),  # K2-free spider
+    gg.from_edge_list(5, [(0, 1), (2, 3), (3, 4)]),                   # K2 component kept
+    # a star (centre isolated in the residual graph, omega = 3) beside a cycle with a leaf
+    gg.from_edge_list(9, [(0, 1), (0, 2), (0, 3), (4, 5), (5, 6), (6, 7), (7, 4), (7, 8)]),
+]
+
+
+@pytest.mark.parametrize("gi", range(len(H3_GRAPHS)))
+def test_bc_deg2_with_pruning_equals_plain(gi):
+    """Both heuristics at once (the paper's H3): triples chosen on the residual graph, leaf
+    weights in every run; the result is exact (Eq. 1 by brute force on small graphs)."""
+    g = H3_GRAPHS[gi]
+    got, ntri = deg2.bc_with_deg2(g, prune=True)
+    want = oracle.bc_exact(g)
+    for v in range(g.n):
+        assert abs(float(got[v]) - want[v]) <= 1e-9 * max(abs(want[v]), 1.0), (g.name, v)
+    if g.n <= 12:
+        ex = brute.bc_enumerate(g)
+        assert all(got[v] == ex[v] for v in range(g.n)), g.name
+    if gi < 4:
+        assert ntri > 0
+
+
+def test_pruning_changes_the_selection():
+    """A cycle with a leaf on every vertex has no degree-2 vertex; its residual graph is the
+    bare cycle, so H3 derives runs that H2 alone could not."""
+    g = gg.attach_leaves(gg.cycle_graph(12), 1.0, 8, max_leaves=1)
+    _, om_tri = deg2.bc_with_deg2(g, prune=True)
+    assert not deg2.select_triples(g) and om_tri > 0
