@@ -434,34 +434,44 @@ def deg2_triples(g) -> int:
 
 
 def deg2_study():
-    """2-degree heuristic (Sec. 3.4.2) on road-network stand-ins small enough for the
-    per-source CTA kernel: all sources, exact BC with and without the heuristic (device
-    time of the call), the number of degree-2 runs derived, and the largest relative
-    difference between the two results."""
+    """The two heuristics of Sec. 3.4 on road-network stand-ins small enough for the
+    per-source CTA kernel, all sources, exact BC: H0 plain, H1 1-degree reduction, H2 the
+    2-degree heuristic, H3 both (device time of the call), the degree-2 runs derived, and
+    the largest relative difference of each result from H0."""
     import paper_1602_00963_gb300 as bc
     ctx = bc.bc_ctx_create(0)
+    sub = gg.subdivide_edges(gg.grid2d(160, 160, seed=18, delete_frac=0.1), 0.4, 19)
     graphs = [("grid 256x256, 10% deleted, LCC", gg.cached("grid", gg.grid2d, 256, 256, 16, 0.1)),
-              ("grid 160x160, 10% deleted, LCC, 40% of edges subdivided",
-               gg.subdivide_edges(gg.grid2d(160, 160, seed=18, delete_frac=0.1), 0.4, 19))]
-    rows = []
+              ("grid 160x160, 10% deleted, LCC, 40% of edges subdivided", sub),
+              ("the same with 1-2 dead ends on 15% of the vertices", gg.attach_leaves(sub, 0.15, 20, 2))]
     P = bc.BC_PATH_PLAIN
+    variants = {"H0": P, "H1": P | bc.BC_PRUNE_DEG1, "H2": P | bc.BC_DEG2,
+                "H3": P | bc.BC_DEG2 | bc.BC_PRUNE_DEG1}
+    rows = []
     for name, g in graphs:
         h = bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0)
         bc.bc_sources(h, g.n, gg.sample_sources(g, 64, seed=1), P)  # workspace set-up
-        bc.bc_exact(h, g.n, P | bc.BC_DEG2)
-        b0, s0 = bc.bc_exact(h, g.n, P)
-        b2, s2 = bc.bc_exact(h, g.n, P | bc.BC_DEG2)
+        res = {}
+        for key, fl in variants.items():
+            bc.bc_exact(h, g.n, fl)  # warm-up (and the 1-degree preprocessing, cached)
+            res[key] = bc.bc_exact(h, g.n, fl)
+        b0, s0 = res["H0"]
         deg = g.degrees()
-        ntri = deg2_triples(g)
-        err = np.abs(b2 - b0) / np.maximum(np.abs(b0), 1.0)
-        rows.append({"graph": name, "n": g.n, "m": g.m, "degree2_vertices": int((deg == 2).sum()),
-                     "derived_runs": ntri, "sources": int((deg > 0).sum()),
-                     "seconds_plain": s0["seconds"], "seconds_deg2": s2["seconds"],
-                     "speedup": s0["seconds"] / s2["seconds"], "gteps_plain": s0["gteps"],
-                     "gteps_deg2": s2["gteps"], "max_rel_diff": float(err.max())})
+        omega, removed, rrp, rci = bc.bc_prune(h, g.n, g.nnz)
+        resg = gg.Graph(g.n, rrp, rci, g.name + "-res")
+        row = {"graph": name, "n": g.n, "m": g.m, "degree1_vertices": int((deg == 1).sum()),
+               "leaves_removed": int(removed.sum()), "degree2_vertices": int((deg == 2).sum()),
+               "derived_runs_H2": deg2_triples(g), "derived_runs_H3": deg2_triples(resg),
+               "sources_H0": int((deg > 0).sum()), "seconds_H0": s0["seconds"]}
+        for key in ("H1", "H2", "H3"):
+            bk, sk = res[key]
+            row[f"seconds_{key}"] = sk["seconds"]
+            row[f"speedup_{key}"] = s0["seconds"] / sk["seconds"]
+            row[f"max_rel_diff_{key}"] = float((np.abs(bk - b0) / np.maximum(np.abs(b0), 1.0)).max())
+        rows.append(row)
         bc.bc_destroy(h)
     bc.bc_destroy(ctx)
-    print(json.dumps({"study": "2-degree heuristic, per-source path (one source per CTA), all sources",
+    print(json.dumps({"study": "heuristics H0-H3, per-source path (one source per CTA), all sources",
                       "rows": rows}), flush=True)
 
 

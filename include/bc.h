@@ -68,8 +68,10 @@ enum {
  * a neighbour or being one, is run without a traversal of its own: the shortest-path DAG of c
  * is derived from those of its two neighbours a, b (run from the same CTA) and c's
  * dependencies are accumulated on it (dynamic merging of frontiers, Alg. 8 / Alg. 9).  The
- * result equals the plain run.  Per-source path on graphs of up to 65,536 vertices only;
- * not with BC_PRUNE_DEG1, BC_PATH_TILED or BC_PLAIN_GRID (BC_EINVAL). */
+ * result equals the plain run.  With BC_PRUNE_DEG1 both heuristics apply (the paper's H3):
+ * the triples are chosen on the residual graph and every run carries the leaf weights.
+ * Per-source path on graphs of up to 65,536 vertices only; not with BC_PATH_TILED or
+ * BC_PLAIN_GRID (BC_EINVAL). */
 #define BC_DEG2           (1u << 12)
 /* bits 8..11: tile width selector for BC_PATH_TILED: 0 = autotuned, else 32 << (k-1) */
 #define BC_TILE_SHIFT     8

@@ -366,13 +366,20 @@ static bc_status full_source_list(Graph *g, const DeviceGraph *dg, int32_t **lis
 
 // 2-degree heuristic (Sec. 3.4.2): pick degree-2 vertices c with neighbours a, b, in vertex
 // order, such that no vertex belongs to two triples; each triple runs a and b and derives c
-// (one CTA), every other non-isolated vertex runs as usual.
-static bc_status run_deg2(Graph *g, double *d_bc, cudaStream_t st, bc_stats *acc) {
+// (one CTA), every other source runs as usual.  With `pruned` (both heuristics, after the
+// 1-degree reduction) the triples are chosen on the residual graph, the sources are the
+// non-removed vertices that have an edge or a leaf, and every run carries the leaf weights.
+static bc_status run_deg2(Graph *g, bool pruned, double *d_bc, cudaStream_t st, bc_stats *acc) {
   Ctx *c = g->ctx;
-  const int32_t n = g->g.n;
-  std::vector<int32_t> rp((size_t)n + 1), ci((size_t)g->g.nnz);
-  BC_CUDA_TRY(cudaMemcpy(rp.data(), g->g.rp, rp.size() * 4, cudaMemcpyDeviceToHost));
-  if (!ci.empty()) BC_CUDA_TRY(cudaMemcpy(ci.data(), g->g.ci, ci.size() * 4, cudaMemcpyDeviceToHost));
+  const DeviceGraph *dg = pruned ? &g->prune.res : &g->g;
+  const int32_t n = dg->n;
+  std::vector<int32_t> rp((size_t)n + 1), ci((size_t)dg->nnz), om;
+  BC_CUDA_TRY(cudaMemcpy(rp.data(), dg->rp, rp.size() * 4, cudaMemcpyDeviceToHost));
+  if (!ci.empty()) BC_CUDA_TRY(cudaMemcpy(ci.data(), dg->ci, ci.size() * 4, cudaMemcpyDeviceToHost));
+  if (pruned) {
+    om.resize((size_t)n);
+    BC_CUDA_TRY(cudaMemcpy(om.data(), g->prune.omega, om.size() * 4, cudaMemcpyDeviceToHost));
+  }
   std::vector<uint8_t> used((size_t)n, 0);
   std::vector<int32_t> tri, single;
   for (int32_t v = 0; v < n; v++) {
@@ -385,7 +392,7 @@ static bc_status run_deg2(Graph *g, double *d_bc, cudaStream_t st, bc_stats *acc
     tri.push_back(v);
   }
   for (int32_t v = 0; v < n; v++)
-    if (rp[v + 1] > rp[v] && !used[v]) single.push_back(v);
+    if (!used[v] && (rp[v + 1] > rp[v] || (pruned && om[v] > 0))) single.push_back(v);
   DevBuf sbuf, tbuf;
   bc_status s = sbuf.get(c, (single.size() + 1) * 4);
   if (!s) s = tbuf.get(c, (tri.size() + 3) * 4);
@@ -395,7 +402,9 @@ static bc_status run_deg2(Graph *g, double *d_bc, cudaStream_t st, bc_stats *acc
   if (!tri.empty())
     BC_CUDA_TRY(cudaMemcpyAsync(tbuf.p, tri.data(), tri.size() * 4, cudaMemcpyHostToDevice, st));
   PlainArgs pa{};
-  pa.g = &g->g;
+  pa.g = dg;
+  pa.omega = pruned ? g->prune.omega : nullptr;
+  pa.leaf_term = pruned;
   pa.src = (const int32_t *)sbuf.p;
   pa.nsrc = (int32_t)single.size();
   pa.tri = (const int32_t *)tbuf.p;
@@ -432,10 +441,14 @@ bc_status bc_exact(bc_graph *graph, uint32_t flags, double *bc_out, void *cuda_s
   bc_stats acc{};
   bc_status s;
   if (flags & BC_DEG2) {
-    if (flags & (BC_PRUNE_DEG1 | BC_PATH_TILED | BC_PLAIN_GRID))
-      return fail(BC_EINVAL, "bc_exact: BC_DEG2 runs on the per-source CTA kernel only, unpruned");
+    if (flags & (BC_PATH_TILED | BC_PLAIN_GRID))
+      return fail(BC_EINVAL, "bc_exact: BC_DEG2 runs on the per-source CTA kernel only");
     if (!cta_fits(n)) return fail(BC_EINVAL, "bc_exact: BC_DEG2 needs a graph of at most 65,536 vertices");
-    s = run_deg2(g, d_bc, st, &acc);
+    if (flags & BC_PRUNE_DEG1) {
+      s = prune_build(c, g, st);
+      if (s) return s;
+    }
+    s = run_deg2(g, (flags & BC_PRUNE_DEG1) != 0, d_bc, st, &acc);
   } else if (flags & BC_PRUNE_DEG1) {
     s = prune_build(c, g, st);
     if (s) return s;

@@ -425,11 +425,14 @@ __device__ __forceinline__ XS deg2_sigma(const CtaState &A, const CtaState &B, i
 // Backward sweep of the 2-degree vertex c on its derived DAG, level by level (the dynamic
 // merging of frontiers, Alg. 8 / Alg. 9): c's level D holds the vertices of a's level D - 1
 // whose level from b is not smaller, and those of b's level D - 1 whose level from a is
-// larger.  rc holds c's r values (scaled by 2^e of sigma_c).  Unpruned graphs only (omega = 0).
+// larger.  rc holds c's r values (scaled by 2^e of sigma_c).  On a residual graph (1-degree
+// reduction) the leaf weights enter as in cta_backward; c, a and b share a component, so the
+// weighted component size sh.ns left by b's forward sweep is also c's.
 __device__ void cta_backward_deg2(const CtaK &p, const CtaState &A, const CtaState &B, int lmaxA, int lmaxB,
-                                  int c, float2 *rc, double *bcp) {
+                                  int c, float2 *rc, double *bcp, const CtaShared &sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int lmax = 1 + (lmaxA > lmaxB ? lmaxA : lmaxB);
+  const float2 wsrc = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[c] : 0ull));
   for (int D = lmax; D >= 1; --D) {
 #pragma unroll 1
     for (int side = 0; side < 2; side++) {
@@ -455,15 +458,20 @@ __device__ void cta_backward_deg2(const CtaK &p, const CtaState &A, const CtaSta
         for (int m = 16; m >= 1; m >>= 1) ff_add(acc, ff_shfl_xor(acc, m));
         if (lane == 0) {
           const float2 mw = ff_mant(sw.m);
-          float2 rw = ff_rcp(mw);
+          const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
+          float2 rw = ff_mul(om1, ff_rcp(mw));
           ff_add(rw, acc);
           rc[w] = rw;
-          const float2 dl = ff_mul(mw, acc);
+          const float2 dl = ff_mul(wsrc, ff_mul(mw, acc));
           if (!ff_zero(dl)) bcp[w] += ff_to(dl);
         }
       }
     }
     __syncthreads();
+  }
+  if (threadIdx.x == 0 && p.leaf_term && p.omega && p.omega[c] > 0) {
+    const double om = (double)p.omega[c];
+    bcp[c] += om * (2.0 * (double)sh.ns - om - 3.0);
   }
 }
 
@@ -529,7 +537,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_cta_sources(CtaK p) {
     const int lb = cta_forward(p, B, b, sh, &qb, &my_arcs);
     account(lb, qb);
     cta_backward(p, B, b, lb, bcp, sh);
-    cta_backward_deg2(p, A, B, la, lb, c, rc, bcp);
+    cta_backward_deg2(p, A, B, la, lb, c, rc, bcp, sh);
     cta_reset(A, qa);
     cta_reset(B, qb);
   }

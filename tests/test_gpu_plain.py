@@ -208,10 +208,32 @@ def test_deg2_heuristic_equals_plain(ctx, gi):
     bc.bc_destroy(h)
 
 
+H3_GRAPHS = [
+    gg.attach_leaves(gg.cycle_graph(60), 1.0, 8, max_leaves=1),  # degree 2 only after pruning
+    gg.attach_leaves(gg.subdivide_edges(gg.grid2d(30, 30, seed=1, delete_frac=0.1), 0.5, 2), 0.3, 3),
+    gg.attach_leaves(gg.subdivide_edges(gg.grid2d(70, 70), 0.05, 7), 0.2, 4),  # past 2^64
+    gg.attach_leaves(gg.subdivide_edges(gg.rmat(10, 4, 5), 0.3, 6), 0.3, 9),
+    gg.from_edge_list(9, [(0, 1), (0, 2), (0, 3), (4, 5), (5, 6), (6, 7), (7, 4), (7, 8)]),
+]
+
+
+@pytest.mark.parametrize("gi", range(len(H3_GRAPHS)))
+def test_deg2_with_pruning_equals_plain(ctx, gi):
+    """BC_DEG2 | BC_PRUNE_DEG1 (both heuristics, the paper's H3): triples on the residual
+    graph, leaf weights in every run and the leaf term for derived sources."""
+    g = H3_GRAPHS[gi]
+    h = upload(ctx, g)
+    got, st = bc.bc_exact(h, g.n, PLAIN | bc.BC_DEG2 | bc.BC_PRUNE_DEG1)
+    assert_bc_close(got, oracle.bc_exact(g, nthreads=8), what=f"{g.name} deg2 pruned")
+    omega, removed, res = oracle.prune_deg1(g)
+    assert st["sources"] == int(((removed == 0) & ((res.degrees() > 0) | (omega > 0))).sum())
+    bc.bc_destroy(h)
+
+
 def test_deg2_flag_rules(ctx):
     g = gg.cycle_graph(12)
     h = upload(ctx, g)
-    for bad in (bc.BC_PRUNE_DEG1, bc.BC_PATH_TILED, bc.BC_PLAIN_GRID):
+    for bad in (bc.BC_PATH_TILED, bc.BC_PLAIN_GRID):
         with pytest.raises(bc.BCError) as e:
             bc.bc_exact(h, g.n, PLAIN | bc.BC_DEG2 | bad)
         assert e.value.status == bc.BC_EINVAL
