@@ -99,6 +99,7 @@ __device__ __forceinline__ CtaState cta_carve(char *blk, char *extra, int n) {
 constexpr int kCtaLaneDeg = 32;  // vertices of degree <= this are handled by one thread
 constexpr int kStage = 4;        // state in global memory: a thread's edges are loaded
                                  // kStage at a time (their latencies overlap)
+constexpr int kStage2 = 2;       // the same for the 2-degree backward sweep
 constexpr int kCtaBig = 512;     // higher-degree vertices listed per pass for whole warps
 
 struct CtaShared {
@@ -168,7 +169,6 @@ __device__ int cta_forward(const CtaK &p, const CtaState &S, int s, CtaShared &s
     sh.q = 1;
     sh.ovf = 0;
     sh.lovf[1] = 0;
-    sh.ns = 1ull + (p.omega ? (unsigned long long)p.omega[s] : 0ull);
   }
   __syncthreads();
   int level = 1, q0 = 0, q1 = 1;
@@ -180,7 +180,6 @@ __device__ int cta_forward(const CtaK &p, const CtaState &S, int s, CtaShared &s
         const int old = atomicCAS(&S.d[w], -1, level);
         if (old < 0) {
           S.Q[atomicAdd(&sh.q, 1)] = w;
-          if (p.leaf_term && p.omega) atomicAdd(&sh.ns, 1ull + (unsigned long long)p.omega[w]);
           dw = level;
         } else {
           dw = old;
@@ -220,7 +219,6 @@ __device__ int cta_forward(const CtaK &p, const CtaState &S, int s, CtaShared &s
               const int old = atomicCAS(&S.d[w[j]], -1, level);
               if (old < 0) {
                 S.Q[atomicAdd(&sh.q, 1)] = w[j];
-                if (p.leaf_term && p.omega) atomicAdd(&sh.ns, 1ull + (unsigned long long)p.omega[w[j]]);
                 dw[j] = level;
               } else {
                 dw[j] = old;
@@ -389,6 +387,19 @@ __device__ void cta_backward(const CtaK &p, const CtaState &S, int s, int lmax, 
   }
 }
 
+// n_s of Eq. 3: the reached vertices Q[0, qtot) weighted by 1 + omega (a source with
+// omega(s) > 0 only; the sum is an integer, so its order does not matter).  Ends with a barrier.
+__device__ void cta_weighted_size(const CtaK &p, const CtaState &S, int qtot, CtaShared &sh) {
+  if (threadIdx.x == 0) sh.ns = 0ull;
+  __syncthreads();
+  unsigned long long part = 0ull;
+  for (int i = threadIdx.x; i < qtot; i += kCtaThreads) part += 1ull + (unsigned long long)p.omega[S.Q[i]];
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) part += __shfl_xor_sync(BC_FULL, part, m);
+  if ((threadIdx.x & 31) == 0 && part) atomicAdd(&sh.ns, part);
+  __syncthreads();
+}
+
 __device__ void cta_reset(const CtaState &S, int qtot) {
   __syncthreads();
   for (int i = threadIdx.x; i < qtot; i += kCtaThreads) {
@@ -422,52 +433,83 @@ __device__ __forceinline__ XS deg2_sigma(const CtaState &A, const CtaState &B, i
   return xs_norm(x);
 }
 
+// exponent of sigma_c(v) as m 2^e (v != c)
+__device__ __forceinline__ int deg2_exp(const CtaState &A, const CtaState &B, int v) {
+  const int da = A.d[v], db = B.d[v];
+  if (db < 0 || (da >= 0 && da < db)) return cta_exp(A, v);
+  if (da < 0 || db < da) return cta_exp(B, v);
+  XS x = cta_sigma(A, v);
+  xs_add(x, cta_sigma(B, v));
+  return xs_norm(x).e;
+}
+
 // Backward sweep of the 2-degree vertex c on its derived DAG, level by level (the dynamic
 // merging of frontiers, Alg. 8 / Alg. 9): c's level D holds the vertices of a's level D - 1
 // whose level from b is not smaller, and those of b's level D - 1 whose level from a is
 // larger.  rc holds c's r values (scaled by 2^e of sigma_c).  On a residual graph (1-degree
 // reduction) the leaf weights enter as in cta_backward; c, a and b share a component, so the
-// weighted component size sh.ns left by b's forward sweep is also c's.
+// weighted component size in sh.ns (set for the triple) is also c's.
 __device__ void cta_backward_deg2(const CtaK &p, const CtaState &A, const CtaState &B, int lmaxA, int lmaxB,
-                                  int c, float2 *rc, double *bcp, const CtaShared &sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+                                  int c, float2 *rc, double *bcp, CtaShared &sh) {
+  const int lane = threadIdx.x & 31;
   const int lmax = 1 + (lmaxA > lmaxB ? lmaxA : lmaxB);
   const float2 wsrc = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[c] : 0ull));
+  auto commit = [&](int w, const XS &sw, float2 acc) {
+    const float2 mw = ff_mant(sw.m);
+    const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
+    float2 rw = ff_mul(om1, ff_rcp(mw));
+    ff_add(rw, acc);
+    rc[w] = rw;
+    const float2 dl = ff_mul(wsrc, ff_mul(mw, acc));
+    if (!ff_zero(dl)) bcp[w] += ff_to(dl);
+  };
   for (int D = lmax; D >= 1; --D) {
 #pragma unroll 1
     for (int side = 0; side < 2; side++) {
       const CtaState &S = side ? B : A;
       const int lm = side ? lmaxB : lmaxA;
       if (D - 1 > lm) continue;
-      const int a0 = S.loff[D - 1], a1 = S.loff[D];
-      for (int i = a0 + wid; i < a1; i += kCtaWarps) {
-        const int w = S.Q[i];
-        if (w == c) continue;
+      // w belongs to c's level D through this side (ties go to a)
+      auto mine = [&](int w) {
+        if (w == c) return false;
         const int da = A.d[w], db = B.d[w];
-        const bool mine = side == 0 ? (db < 0 || da <= db) : (da < 0 || db < da);
-        if (!mine) continue;
-        const XS sw = deg2_sigma(A, B, c, w);
-        float2 acc = make_float2(0.0f, 0.0f);
-        const int e1 = p.rp[w + 1];
-        for (int e = p.rp[w] + lane; e < e1; e += 32) {
-          const int v = p.ci[e];
-          if (deg2_level(A, B, c, v) != D + 1) continue;
-          ff_add(acc, ff_scale(rc[v], sw.e - deg2_sigma(A, B, c, v).e));
-        }
+        return side == 0 ? (db < 0 || da <= db) : (da < 0 || db < da);
+      };
+      cta_split(
+          p, S.Q, S.loff[D - 1], S.loff[D], sh,
+          [&](int w) {
+            if (!mine(w)) return;
+            const XS sw = deg2_sigma(A, B, c, w);
+            float2 acc = make_float2(0.0f, 0.0f);
+            const int e1 = p.rp[w + 1];
+            for (int e = p.rp[w]; e < e1; e += kStage2) {
+              int v[kStage2];
+              bool suc[kStage2];
 #pragma unroll
-        for (int m = 16; m >= 1; m >>= 1) ff_add(acc, ff_shfl_xor(acc, m));
-        if (lane == 0) {
-          const float2 mw = ff_mant(sw.m);
-          const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
-          float2 rw = ff_mul(om1, ff_rcp(mw));
-          ff_add(rw, acc);
-          rc[w] = rw;
-          const float2 dl = ff_mul(wsrc, ff_mul(mw, acc));
-          if (!ff_zero(dl)) bcp[w] += ff_to(dl);
-        }
-      }
+              for (int j = 0; j < kStage2; j++) v[j] = e + j < e1 ? p.ci[e + j] : -1;
+#pragma unroll
+              for (int j = 0; j < kStage2; j++) suc[j] = v[j] >= 0 && deg2_level(A, B, c, v[j]) == D + 1;
+#pragma unroll
+              for (int j = 0; j < kStage2; j++)
+                if (suc[j]) ff_add(acc, ff_scale(rc[v[j]], sw.e - deg2_exp(A, B, v[j])));
+            }
+            commit(w, sw, acc);
+          },
+          [&](int w) {
+            if (!mine(w)) return;
+            const XS sw = deg2_sigma(A, B, c, w);
+            float2 acc = make_float2(0.0f, 0.0f);
+            const int e1 = p.rp[w + 1];
+            for (int e = p.rp[w] + lane; e < e1; e += 32) {
+              const int v = p.ci[e];
+              if (deg2_level(A, B, c, v) != D + 1) continue;
+              ff_add(acc, ff_scale(rc[v], sw.e - deg2_exp(A, B, v)));
+            }
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) ff_add(acc, ff_shfl_xor(acc, m));
+            if (lane == 0) commit(w, sw, acc);
+          });
     }
-    __syncthreads();
   }
   if (threadIdx.x == 0 && p.leaf_term && p.omega && p.omega[c] > 0) {
     const double om = (double)p.omega[c];
@@ -516,6 +558,7 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_cta_sources(CtaK p) {
     int qtot = 0;
     const int lmax = cta_forward(p, A, s, sh, &qtot, &my_arcs);
     account(lmax, qtot);
+    if (p.leaf_term && p.omega && p.omega[s] > 0) cta_weighted_size(p, A, qtot, sh);
     if (p.out_depth) {  // forward-only export (sssp of src[0])
       for (int v = tid; v < n; v += kCtaThreads) {
         p.out_depth[v] = A.d[v];
@@ -533,6 +576,9 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_cta_sources(CtaK p) {
     int qa = 0, qb = 0;
     const int la = cta_forward(p, A, a, sh, &qa, &my_arcs);
     account(la, qa);
+    // a, b and c share a component: one weighted size serves all three
+    if (p.leaf_term && p.omega && (p.omega[a] > 0 || p.omega[b] > 0 || p.omega[c] > 0))
+      cta_weighted_size(p, A, qa, sh);
     cta_backward(p, A, a, la, bcp, sh);
     const int lb = cta_forward(p, B, b, sh, &qb, &my_arcs);
     account(lb, qb);
