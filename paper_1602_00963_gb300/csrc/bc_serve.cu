@@ -142,8 +142,10 @@ void admit(Server *sv) {
       continue;
     }
     bc_status s = c->mem.alloc((void **)&r->d_bc, (size_t)r->g->g.n * 8);
-    if (!s && cudaMemset(r->d_bc, 0, (size_t)r->g->g.n * 8) != cudaSuccess)
-      s = fail(BC_ECUDA, "serving: cudaMemset");
+    // zeroed before a worker's stream (non-blocking, so unordered with this one) adds to it
+    if (!s && (cudaMemsetAsync(r->d_bc, 0, (size_t)r->g->g.n * 8, nullptr) != cudaSuccess ||
+               cudaStreamSynchronize(nullptr) != cudaSuccess))
+      s = fail(BC_ECUDA, "serving: clearing a request's result buffer");
     r->admitted = true;
     sv->active.push_back(r);
     if (s || r->src.empty()) {

@@ -2148,7 +2148,7 @@ void tile_free(Ctx *ctx, TileWS *ws) {
     if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), b_ != 0 ? b_ : (size_t)16);     \
   } while (0)
 
-static bc_status ws_main(Ctx *ctx, TileWS *ws, int n, int T) {
+static bc_status ws_main(Ctx *ctx, TileWS *ws, int n, int T, cudaStream_t st) {
   if (ws->ctl && ws->n == n && ws->T == T) return BC_OK;
   ws_release(ctx, ws, true, true, true);
   const int G = T / 32;
@@ -2181,7 +2181,10 @@ static bc_status ws_main(Ctx *ctx, TileWS *ws, int n, int T) {
     ws_release(ctx, ws, true, false, false);
     return fail(BC_ENOMEM, std::string("tile workspace allocation failed: ") + cudaGetErrorString(e));
   }
-  BC_CUDA_TRY(cudaMemset(ws->cand, 0, (N / 32 + 1) * 4));
+  // cleared before any launch on any stream uses it (a plain cudaMemset may still be
+  // running when the host goes on, and callers' streams need not sync with its stream)
+  BC_CUDA_TRY(cudaMemsetAsync(ws->cand, 0, (N / 32 + 1) * 4, st));
+  BC_CUDA_TRY(cudaStreamSynchronize(st));
   return BC_OK;
 }
 
@@ -2470,7 +2473,7 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
     if (!*wsp) return fail(BC_ENOMEM, "host allocation failed");
   }
   TileWS *ws = *wsp;
-  bc_status s = ws_main(ctx, ws, dg->n, a.T);
+  bc_status s = ws_main(ctx, ws, dg->n, a.T, st);
   if (!s) s = ws_lists(ctx, ws, dg, st);
   if (!s) s = ws_hpart(ctx, ws, dg->nnz);
   if (s) return s;
