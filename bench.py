@@ -50,10 +50,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sources", type=int, default=4096)
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
-    ap.add_argument("--study", default=None, choices=["deg1", "deg2"],
+    ap.add_argument("--study", default=None, choices=["deg1", "deg2", "scan"],
                     help="deg1: the 1-degree removal study on R-MAT scale 20, EF 4 / 16 / 32; "
-                         "deg2: the 2-degree heuristic on road-like graphs (one JSON line, "
-                         "instead of the benchmark)")
+                         "deg2: the heuristics H0-H3 on road-like graphs; scan: the degree-prefix "
+                         "reuse of the per-source path on and off (one JSON line, instead of the "
+                         "benchmark)")
     ap.add_argument("--profile-case", default=None,
                     help="run one small case for a profiler and exit: 'tile:T:K' (one bc_sources "
                          "call of K sources in tiles of T) or 'plain:K' on the R-MAT scale-20 graph")
@@ -475,6 +476,38 @@ def deg2_study():
                       "rows": rows}), flush=True)
 
 
+def scan_study():
+    """Sec. 3.1's reuse of the forward sweep's degree prefix CD in the backward sweep,
+    measured on the grid-wide per-source kernel: the same sources with the reuse and with
+    CD scanned again per backward level (BC_NO_CD_REUSE), device time of the call, on a
+    short-diameter R-MAT and on long-diameter grids (the paper's comparison of Sec. 4)."""
+    import paper_1602_00963_gb300 as bc
+    ctx = bc.bc_ctx_create(0)
+    cases = [("R-MAT scale 16, EF 16, seed 5", gg.rmat(16, 16, 5), 256),
+             ("grid 256x256, 10% deleted, LCC", gg.cached("grid", gg.grid2d, 256, 256, 16, 0.1), 64),
+             ("grid 1024x1024, 10% deleted, LCC", gg.cached("grid", gg.grid2d, 1024, 1024, 5, 0.1), 16)]
+    G = bc.BC_PATH_PLAIN | bc.BC_PLAIN_GRID
+    rows = []
+    for name, g, k in cases:
+        src = gg.sample_sources(g, k, seed=7)
+        h = bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0)
+        res = {}
+        for key, fl in (("reuse", G), ("rescan", G | bc.BC_NO_CD_REUSE)):
+            bc.bc_sources(h, g.n, src[:4], fl)
+            res[key] = bc.bc_sources(h, g.n, src, fl)
+        (b0, s0), (b1, s1) = res["reuse"], res["rescan"]
+        rows.append({"graph": name, "n": g.n, "m": g.m, "sources": k,
+                     "levels_per_source": s0["levels"] / k,
+                     "seconds_reuse": s0["seconds"], "seconds_rescan": s1["seconds"],
+                     "gain_of_reuse": s1["seconds"] / s0["seconds"] - 1.0,
+                     "gteps_reuse": s0["gteps"], "gteps_rescan": s1["gteps"],
+                     "max_rel_diff": float((np.abs(b1 - b0) / np.maximum(np.abs(b0), 1.0)).max())})
+        bc.bc_destroy(h)
+    bc.bc_destroy(ctx)
+    print(json.dumps({"study": "degree-prefix reuse (Sec. 3.1), grid-wide per-source kernel",
+                      "rows": rows}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -487,6 +520,9 @@ def main():
         return
     if args.study == "deg2":
         deg2_study()
+        return
+    if args.study == "scan":
+        scan_study()
         return
     if args.impl == "reference":
         if world > 1:

@@ -73,6 +73,12 @@ enum {
  * Per-source path on graphs of up to 65,536 vertices only; not with BC_PATH_TILED or
  * BC_PLAIN_GRID (BC_EINVAL). */
 #define BC_DEG2           (1u << 12)
+/* bc_exact / bc_sources, grid-wide per-source kernel only (needs BC_PATH_PLAIN |
+ * BC_PLAIN_GRID, else BC_EINVAL): the backward sweep scans each level's degree prefix CD
+ * again instead of reusing the one the forward sweep stored (Sec. 3.1's reuse switched off,
+ * for measuring it).  The prefix values are the same, so the result differs only by the
+ * order of the kernel's floating-point atomic additions. */
+#define BC_NO_CD_REUSE    (1u << 14)
 /* bits 8..11: tile width selector for BC_PATH_TILED: 0 = autotuned, else 32 << (k-1) */
 #define BC_TILE_SHIFT     8
 #define BC_TILE_MASK      (0xFu << BC_TILE_SHIFT)

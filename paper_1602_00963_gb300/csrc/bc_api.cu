@@ -168,6 +168,9 @@ bc_status run_sources(Graph *g, const int32_t *d_src, int32_t k, uint32_t flags,
                       const int32_t *omega, bool leaf_term, double *d_bc, cudaStream_t st,
                       bc_stats *stats, const DeviceGraph *dg) {
   Ctx *ctx = g->ctx;
+  if ((flags & BC_NO_CD_REUSE) && (flags & (BC_PATH_PLAIN | BC_PLAIN_GRID)) != (BC_PATH_PLAIN | BC_PLAIN_GRID))
+    return fail(BC_EINVAL, "BC_NO_CD_REUSE applies to the grid-wide per-source kernel only "
+                           "(BC_PATH_PLAIN | BC_PLAIN_GRID)");
   if (k <= 0) return BC_OK;
   bool tiled = (flags & BC_PATH_TILED) != 0;
   bool plain = (flags & BC_PATH_PLAIN) != 0;
@@ -217,6 +220,7 @@ bc_status run_sources(Graph *g, const int32_t *d_src, int32_t k, uint32_t flags,
   pa.max_degree = g->max_degree;
   pa.alpha = alpha;
   pa.beta = beta;
+  pa.no_cd_reuse = (flags & BC_NO_CD_REUSE) != 0;
   const bool want_cta = (flags & BC_PLAIN_CTA) || (!(flags & BC_PATH_PLAIN) && g->tune.ready && g->tune.res.plain_cta);
   if (!(flags & BC_PLAIN_GRID) && (cta_fits(dg->n) || (want_cta && dg->n <= kCtaForcedMaxN)))
     return cta_run(ctx, g, &g->cta, pa, st, stats);
@@ -441,7 +445,7 @@ bc_status bc_exact(bc_graph *graph, uint32_t flags, double *bc_out, void *cuda_s
   bc_stats acc{};
   bc_status s;
   if (flags & BC_DEG2) {
-    if (flags & (BC_PATH_TILED | BC_PLAIN_GRID))
+    if (flags & (BC_PATH_TILED | BC_PLAIN_GRID | BC_NO_CD_REUSE))
       return fail(BC_EINVAL, "bc_exact: BC_DEG2 runs on the per-source CTA kernel only");
     if (!cta_fits(n)) return fail(BC_EINVAL, "bc_exact: BC_DEG2 needs a graph of at most 65,536 vertices");
     if (flags & BC_PRUNE_DEG1) {

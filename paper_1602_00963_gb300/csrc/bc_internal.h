@@ -40,6 +40,7 @@ struct DevMem {
 };
 
 // Control block of one traversal workspace (device memory).
+constexpr int kPlainScanBlocks = 1024;  // CTAs of the per-source kernel the rescan supports
 struct PlainCtl {
   unsigned long long qpack;  // packed queue/edge append counter
   unsigned long long ns;     // component size incl. removed leaves (Eq. 3's n)
@@ -54,6 +55,7 @@ struct PlainCtl {
   long long reached_arcs;
   int trace_n;
   int pad1;
+  int scan_blk[kPlainScanBlocks];  // per-CTA degree sums of a level (BC_NO_CD_REUSE)
 };
 
 // Per-source path workspace for a graph of n vertices (Sec. 3.1/3.2 data structures:
@@ -153,6 +155,9 @@ struct PlainArgs {
   // c's DAG derived from those of a and b (device, 3 ints each)
   const int32_t *tri;
   int32_t ntri;
+  // grid-wide kernel only: rescan each level's degree prefix in the backward sweep
+  // instead of reusing the forward's (ablation of Sec. 3.1's reuse)
+  bool no_cd_reuse;
 };
 bc_status plain_ensure(Ctx *ctx, PlainWS *ws, int32_t n);
 void plain_free(Ctx *ctx, PlainWS *ws);

@@ -73,6 +73,7 @@ struct PK {
   uint64_t limit_ns;
   unsigned long long *trace;  // optional phase trace: (phase << 56 | level << 32, time) pairs
   int trace_cap;
+  int no_cd_reuse;            // backward: rescan CD per level (ablation)
 };
 
 // Grid barrier; with tracing on, CTA 0 stamps the time at which every CTA has finished
@@ -414,6 +415,74 @@ __device__ void finalize_level(const PK &p, int q0, int q1, double ws, int gtid,
   }
 }
 
+// Exclusive prefix of x over the CTA's threads in thread order; *total = the CTA's sum.
+// Contains barriers: every thread of the CTA calls it.
+__device__ __forceinline__ int cta_excl_scan(int x, int *total, int *s_warp) {
+  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  int wt;
+  const int pre = warp_excl_scan(x, &wt);
+  if (lane == 0) s_warp[wid] = wt;
+  __syncthreads();
+  if (wid == 0) {
+    const int v = lane < kWarps ? s_warp[lane] : 0;
+    int t;
+    const int vp = warp_excl_scan(v, &t);
+    if (lane < kWarps) s_warp[lane] = vp;
+    if (lane == 0) s_warp[kWarps] = t;
+  }
+  __syncthreads();
+  const int r = s_warp[wid] + pre;
+  *total = s_warp[kWarps];
+  __syncthreads();  // s_warp is reused by the next call
+  return r;
+}
+
+// Sec. 3.1 without its reuse (the ablation BC_NO_CD_REUSE): before the backward sweep reads
+// the degree prefix CD of level d's entries Q[q0, q1), it is scanned again instead of taken
+// from the forward appends.  CTAs sum the degrees of equal chunks of the level, then each
+// scans its chunk starting from E0 plus the sums of the CTAs before it.  The values equal
+// the stored ones (the appends lay entries and their edge offsets out in queue order), so
+// only the time differs (and the order of the backward's atomic additions).  Two grid
+// barriers.
+__device__ bool rescan_level(const PK &p, GridSync *gs, int d, int q0, int q1, int E0) {
+  __shared__ int s_warp[kWarps + 1];
+  __shared__ int s_base;
+  const int nb = gridDim.x, b = blockIdx.x;
+  const long long len = (long long)q1 - q0;
+  const int c0 = q0 + (int)(len * b / nb), c1 = q0 + (int)(len * (b + 1) / nb);
+  int part = 0;
+  for (int i = c0 + (int)threadIdx.x; i < c1; i += kThreads) {
+    const int v = p.Q[i];
+    part += p.rp[v + 1] - p.rp[v];
+  }
+  int tot;
+  (void)cta_excl_scan(part, &tot, s_warp);
+  if (threadIdx.x == 0) p.ctl->scan_blk[b] = tot;
+  if (!phase_sync(p, gs, 8, d)) return false;
+  if (threadIdx.x < 32) {
+    int acc = 0;
+    for (int j = (int)threadIdx.x; j < b; j += 32) acc += ld_volatile_i32(&p.ctl->scan_blk[j]);
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) acc += __shfl_xor_sync(BC_FULL, acc, m);
+    if (threadIdx.x == 0) s_base = E0 + acc;
+  }
+  __syncthreads();
+  int base = s_base;
+  for (int i0 = c0; i0 < c1; i0 += kThreads) {  // c0, c1 are uniform over the CTA
+    const int i = i0 + (int)threadIdx.x;
+    int dg = 0;
+    if (i < c1) {
+      const int v = p.Q[i];
+      dg = p.rp[v + 1] - p.rp[v];
+    }
+    int t;
+    const int pre = cta_excl_scan(dg, &t, s_warp);
+    if (i < c1) p.CD[i] = base + pre;
+    base += t;
+  }
+  return phase_sync(p, gs, 9, d);
+}
+
 __global__ void __launch_bounds__(kThreads, 1) plain_kernel(PK p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_sig[kWarps][32];
@@ -538,6 +607,7 @@ __global__ void __launch_bounds__(kThreads, 1) plain_kernel(PK p) {
         for (int d = D - 1; d >= 1; --d) {
           const int q0 = p.lvl_off[d], q1 = p.lvl_off[d + 1];
           const int E0 = p.lvl_eoff[d], E1 = p.lvl_eoff[d + 1];
+          if (p.no_cd_reuse && !rescan_level(p, gs, d, q0, q1, E0)) return;
           if (ext)
             accumulate_level<true>(p, W, d, q0, q1, E0, E1, gwarp, nwarps);
           else
@@ -734,6 +804,9 @@ bc_status plain_run(Ctx *ctx, PlainWS *ws, const PlainArgs &a, cudaStream_t st, 
   p.limit_ns = ctx->wait_limit_ns;
   p.trace = nullptr;
   p.trace_cap = 0;
+  p.no_cd_reuse = a.no_cd_reuse ? 1 : 0;
+  if (a.no_cd_reuse && ctx->num_sms * g_blocks_per_sm > kPlainScanBlocks)
+    return fail(BC_EINVAL, "BC_NO_CD_REUSE: more CTAs than the rescan supports");
   static const char *trace_file = getenv("BC_TRACE_FILE");
   if (trace_file) {
     p.trace_cap = 1 << 20;

@@ -230,6 +230,37 @@ def test_deg2_with_pruning_equals_plain(ctx, gi):
     bc.bc_destroy(h)
 
 
+NO_REUSE_GRAPHS = [gg.rmat(12, 16, 1), gg.grid2d(40, 40, seed=5, delete_frac=0.1), gg.path_graph(300)]
+
+
+@pytest.mark.parametrize("gi", range(len(NO_REUSE_GRAPHS)))
+def test_no_cd_reuse_same_result(ctx, gi):
+    """BC_NO_CD_REUSE (the degree prefix CD scanned again per backward level, Sec. 3.1's
+    reuse switched off): same BC as with the reuse (up to the atomics' order) and as the
+    oracle, pruned and unpruned."""
+    g = NO_REUSE_GRAPHS[gi]
+    h = upload(ctx, g)
+    GRID = PLAIN | bc.BC_PLAIN_GRID
+    want = oracle.bc_exact(g, nthreads=8)
+    for extra in (0, bc.BC_PRUNE_DEG1):
+        a, _ = bc.bc_exact(h, g.n, GRID | extra)
+        b, _ = bc.bc_exact(h, g.n, GRID | extra | bc.BC_NO_CD_REUSE)
+        assert np.all(np.abs(a - b) <= 1e-12 * np.maximum(np.abs(a), 1.0)), (g.name, extra)
+        assert_bc_close(b, want, what=f"{g.name} no CD reuse {extra}")
+    bc.bc_destroy(h)
+
+
+def test_no_cd_reuse_flag_rules(ctx):
+    g = gg.cycle_graph(12)
+    h = upload(ctx, g)
+    for bad in (PLAIN, bc.BC_PATH_TILED, bc.BC_PLAIN_GRID, PLAIN | bc.BC_PLAIN_CTA,
+                PLAIN | bc.BC_DEG2):
+        with pytest.raises(bc.BCError) as e:
+            bc.bc_exact(h, g.n, bad | bc.BC_NO_CD_REUSE)
+        assert e.value.status == bc.BC_EINVAL
+    bc.bc_destroy(h)
+
+
 def test_deg2_flag_rules(ctx):
     g = gg.cycle_graph(12)
     h = upload(ctx, g)
