@@ -159,7 +159,7 @@ __device__ void cta_clear(const CtaState &S, int n) {
 // level; *qtot = reached vertices, *arcs += their adjacency entries (lane 0 of each warp).
 __device__ int cta_forward(const CtaK &p, const CtaState &S, int s, CtaShared &sh, int *qtot,
                            unsigned long long *arcs) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) {
     S.d[s] = 0;
     S.sig[s] = 1ull;
@@ -320,7 +320,7 @@ __device__ int cta_forward(const CtaK &p, const CtaState &S, int s, CtaShared &s
 // Backward sweep of s (Alg. 4 / Alg. 5): sigma of w taken as m 2^e, r stored scaled by 2^e.
 __device__ void cta_backward(const CtaK &p, const CtaState &S, int s, int lmax, double *bcp,
                              CtaShared &sh) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   const float2 wsrc = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[s] : 0ull));
   for (int dd = lmax; dd >= 1; --dd) {
     // commit of w from the sum of its successors' r (rescaled to w's exponent)
