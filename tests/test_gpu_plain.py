@@ -269,3 +269,41 @@ def test_deg2_flag_rules(ctx):
             bc.bc_exact(h, g.n, PLAIN | bc.BC_DEG2 | bad)
         assert e.value.status == bc.BC_EINVAL
     bc.bc_destroy(h)
+
+
+def _edgeless(n):
+    return gg.Graph(n, np.zeros(n + 1, np.int32), np.zeros(0, np.int32))
+
+
+def test_degenerate_inputs(ctx):
+    """An empty source list, isolated sources mixed with others (duplicates included), a
+    graph without edges and a single vertex: BC is that of the oracle (zero where nothing
+    is reached) and a lone root has depth 0 and one path, on every path and heuristic."""
+    T = bc.BC_PATH_TILED
+    paths = [PLAIN, PLAIN | bc.BC_PLAIN_GRID, T | bc.BC_TILE(32),
+             T | bc.BC_TILE(64) | bc.BC_LOOP_LAUNCH, T | bc.BC_TILE(32) | bc.BC_LOOP_GRAPH]
+    g = gg.from_edge_list(9, [(0, 1), (1, 2), (2, 3), (5, 6)])  # 4, 7, 8 isolated
+    h = upload(ctx, g)
+    src = np.array([4, 1, 7, 7, 5, 8, 1], np.int32)
+    want = oracle.bc(g, src)
+    for fl in paths:
+        got, st = bc.bc_sources(h, g.n, np.zeros(0, np.int32), fl)
+        assert not got.any() and st["sources"] == 0, fl
+        got, st = bc.bc_sources(h, g.n, src, fl)
+        assert st["sources"] == src.size, fl
+        assert_bc_close(got, want, what=f"isolated sources {fl}")
+    bc.bc_destroy(h)
+    for n in (1, 5):
+        g0 = _edgeless(n)
+        h = upload(ctx, g0)
+        for fl in (PLAIN, PLAIN | bc.BC_PLAIN_GRID, T | bc.BC_TILE(32), PLAIN | bc.BC_PRUNE_DEG1,
+                   PLAIN | bc.BC_DEG2, PLAIN | bc.BC_DEG2 | bc.BC_PRUNE_DEG1):
+            got, _ = bc.bc_exact(h, n, fl)
+            assert not got.any(), (n, fl)
+        for fl in (PLAIN, PLAIN | bc.BC_PLAIN_GRID):
+            got, st = bc.bc_sources(h, n, np.array([n - 1, 0, n - 1], np.int32), fl)
+            assert not got.any() and st["sources"] == 3, (n, fl)
+            d, s, o = bc.bc_sssp(h, n, n - 1, fl)
+            assert d.tolist() == [-1] * (n - 1) + [0], (n, fl)
+            assert s.tolist() == [0] * (n - 1) + [1] and not o.any(), (n, fl)
+        bc.bc_destroy(h)
