@@ -210,7 +210,12 @@ extern "C" bc_status bc_autotune(bc_graph *graph, int32_t probe_sources, uint64_
     c->mem.release(pr.d_src, hs.size() * 4 + 4);
     return s;
   }
-  cudaMemcpy(pr.d_src, hs.data(), hs.size() * 4, cudaMemcpyHostToDevice);
+  const cudaError_t ce = cudaMemcpy(pr.d_src, hs.data(), hs.size() * 4, cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    c->mem.release(pr.d_src, hs.size() * 4 + 4);
+    c->mem.release(pr.d_bc, (size_t)g->g.n * 8);
+    return cuda_fail(ce, "bc_autotune: copy of the probe sources");
+  }
   double best = 1e30, t;
   int bestT = 64, bestMode = 0;
   float bestA = 0.2f;
