@@ -46,22 +46,28 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def load_from(path: str):
+    """ctypes handle of a compiled brandes.c at `path`, with its signatures declared (the
+    tests also load deliberately broken copies this way, to show that the pins catch them)."""
+    lib = ctypes.CDLL(path)
+    lib.oracle_sssp.restype = ctypes.c_int32
+    lib.oracle_sssp.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32,
+                                _i32p, _u64p, _u8p, ctypes.c_void_p]
+    lib.oracle_bc.restype = ctypes.c_int
+    lib.oracle_bc.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.c_int64,
+                              ctypes.c_void_p, _f64p, ctypes.c_int]
+    lib.oracle_prune_deg1.restype = ctypes.c_int
+    lib.oracle_prune_deg1.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, _u8p, _i32p,
+                                      _i32p, ctypes.POINTER(ctypes.c_int64)]
+    lib.oracle_long_double_size.restype = ctypes.c_int
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
-        lib.oracle_sssp.restype = ctypes.c_int32
-        lib.oracle_sssp.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32,
-                                    _i32p, _u64p, _u8p, ctypes.c_void_p]
-        lib.oracle_bc.restype = ctypes.c_int
-        lib.oracle_bc.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, ctypes.c_int64,
-                                  ctypes.c_void_p, _f64p, ctypes.c_int]
-        lib.oracle_prune_deg1.restype = ctypes.c_int
-        lib.oracle_prune_deg1.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p, _u8p, _i32p,
-                                          _i32p, ctypes.POINTER(ctypes.c_int64)]
-        lib.oracle_long_double_size.restype = ctypes.c_int
-        _lib = lib
+        _lib = load_from(_LIB)
     return _lib
 
 
