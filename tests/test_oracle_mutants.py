@@ -104,3 +104,50 @@ def test_planted_mistake_is_caught(swap_lib, name, old, new):
     with tempfile.TemporaryDirectory() as tmp:
         swap_lib(compiled(src.replace(old, new), tmp, "mut"))
         assert not pins_hold(), f"the pins accept the mutant '{name}'"
+
+
+# ---- the 2-degree oracle (oracle/deg2.py): mutated copies run as separate modules
+DEG2_SRC = os.path.join(os.path.dirname(oracle.__file__), "deg2.py")
+DEG2_MUTANTS = [
+    ("tie drops b's paths", "lvl[v], sig[v] = la[v] + 1, sa[v] + sb[v]", "lvl[v], sig[v] = la[v] + 1, sa[v]"),
+    ("derived level off by one", "lvl[v], sig[v] = la[v] + 1, sa[v]\n", "lvl[v], sig[v] = la[v], sa[v]\n"),
+    ("tie goes to a", "elif lb[v] < 0 or (la[v] >= 0 and la[v] < lb[v]):", "elif lb[v] < 0 or (la[v] >= 0 and la[v] <= lb[v]):"),
+    ("dropped omega in the recursion", "(1 + om[v] + delta[v])", "(1 + delta[v])"),
+    ("source's own dependency kept", "    delta[s] = Fraction(0)\n", "\n"),
+    ("source weight without +1", "bc[v] += (om[s] + 1) * d[v]", "bc[v] += d[v]"),
+    ("post-increment reading of Eq. 3", "om[s] * (2 * n_s - om[s] - 3)", "om[s] * (2 * n_s - om[s] - 5)"),
+    ("triples share vertices", "if used[c] or used[a] or used[b]:", "if used[c]:"),
+]
+DEG2_GRAPHS = [gg.cycle_graph(9), gg.subdivide_edges(gg.grid2d(4, 4, seed=1, delete_frac=0.1), 0.5, 2),
+               gg.attach_leaves(gg.cycle_graph(10), 1.0, 8, max_leaves=1),
+               gg.attach_leaves(gg.subdivide_edges(gg.gnm(10, 16, 4), 0.4, 5), 0.4, 6)]
+DEG2_EXACT = [brute.bc_bellman(g) for g in DEG2_GRAPHS]
+
+
+def deg2_module(text: str):
+    import types
+    m = types.ModuleType("deg2_variant")
+    exec(compile(text, DEG2_SRC, "exec"), m.__dict__)
+    return m
+
+
+def deg2_pins_hold(m) -> bool:
+    for g, want in zip(DEG2_GRAPHS, DEG2_EXACT):
+        for prune in (False, True):
+            got, _ = m.bc_with_deg2(g, prune=prune)
+            if list(got) != list(want):
+                return False
+    tri = m.select_triples(gg.subdivide_edges(gg.grid2d(6, 6, seed=3, delete_frac=0.1), 0.6, 4))
+    seen = [v for t in tri for v in t]
+    return len(seen) == len(set(seen))
+
+
+def test_deg2_unmodified_passes():
+    assert deg2_pins_hold(deg2_module(open(DEG2_SRC).read()))
+
+
+@pytest.mark.parametrize("name,old,new", DEG2_MUTANTS, ids=[m[0] for m in DEG2_MUTANTS])
+def test_deg2_planted_mistake_is_caught(name, old, new):
+    src = open(DEG2_SRC).read()
+    assert src.count(old) == 1, f"mutation site not unique: {old!r}"
+    assert not deg2_pins_hold(deg2_module(src.replace(old, new))), f"the pins accept '{name}'"
