@@ -223,9 +223,10 @@ const char *bc_version(void);
  * device pointer owned by the caller; bc_out[n] is overwritten.  Working storage is one
  * static device array of about 3.7 MB, sized for BC_NOALLOC_MAX_N vertices, that every
  * GPU loading the library holds until the process exits; the call allocates nothing,
- * clears that array at its start and returns when the result is complete.  Calls share
- * the array: calls from this process are serialised, but calls whose GPU work overlaps
- * (e.g. from several processes on one device) race.  The first call on a device looks
+ * clears that array at its start and returns when the result is complete.  Calls in one
+ * process share the array and are serialised (one runs at a time, to completion); each
+ * process has its own copy of it, so calls in different processes never share it.  The
+ * first call on a device looks
  * up the array's device address with that device current: make it before any stream
  * capture.  n > BC_NOALLOC_MAX_N returns BC_EINVAL. */
 #define BC_NOALLOC_MAX_N 65536

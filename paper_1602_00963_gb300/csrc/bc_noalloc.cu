@@ -13,10 +13,10 @@
 //   * n <= BC_NOALLOC_MAX_N; larger graphs are rejected with BC_EINVAL.
 //   * The scratch (about 3.7 MB) is part of the library image: every GPU on which the
 //     library is loaded holds it until the process exits.
-//   * All calls share the one array.  The entry point clears what must start cleared at
-//     the beginning of every call and serialises calls made from this process, but two
-//     calls whose work overlaps on the GPU (e.g. issued by several processes sharing a
-//     device) would race on it.
+//   * All calls of a process share the one array.  The entry point clears what must start
+//     cleared at the beginning of every call and holds a lock until the call's work is
+//     complete, so one call runs at a time.  Each process gets its own copy of the array
+//     (a module global lives in the process's own CUDA context).
 //   * The first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress) with that device current; make that first call before any
 //     stream capture.
