@@ -146,16 +146,21 @@ def test_tile_hubs_exact(ctx):
     bc.bc_destroy(h)
 
 
-def test_tile_hub_chunks_exact(ctx):
-    """Hubs of degree 10,000 and 9,000 (three chunks each, spread over CTAs, partial sums
-    combined by the last chunk) plus a sparse part, at both tile widths and loop modes."""
+def hub_chunk_graph():
+    """Hubs of degree 10,000 and 9,000 (three backward chunks each) plus a sparse part."""
     rng = np.random.Generator(np.random.PCG64(12))
     n = 14000
     e = [(0, i) for i in range(1, 10001)] + [(10001, i) for i in range(4000, 13001)]
     u = rng.integers(0, n, 9000)
     v = rng.integers(0, n, 9000)
     e += list(zip(u.tolist(), v.tolist()))
-    g = gg.from_edge_list(n, e)
+    return gg.from_edge_list(n, e)
+
+
+def test_tile_hub_chunks_exact(ctx):
+    """Hubs of degree 10,000 and 9,000 (three chunks each, spread over CTAs, partial sums
+    combined by the last chunk) plus a sparse part, at both tile widths and loop modes."""
+    g = hub_chunk_graph()
     h = upload(ctx, g)
     src = np.arange(3, g.n, 211, dtype=np.int32)
     want = oracle.bc(g, src, nthreads=8)
@@ -206,4 +211,33 @@ def test_tile_timeout_then_recovery(ctx):
         bc.bc_set_wait_limit_ms(ctx, 20000)
     got, _ = bc.bc_exact(h, g.n, TILED | bc.BC_TILE(32))
     assert_bc_close(got, oracle.bc_exact(g), what="after timeout")
+    bc.bc_destroy(h)
+
+
+def test_repeat_runs_bit_identical(ctx):
+    """The tile path and the per-source CTA kernel sum in fixed orders (hub chunks combined
+    in chunk order, per-CTA partials in CTA order), so repeated calls give bit-identical BC;
+    depth, sigma and the overflow flags are identical on every path.  (The grid-wide
+    per-source kernel adds warp segments with FP64 atomics and is excluded.)"""
+    g = gg.rmat(12, 16, 1)
+    h = upload(ctx, g)
+    src = gg.sample_sources(g, 200, seed=3)
+    for fl in (TILED | bc.BC_TILE(64), TILED | bc.BC_TILE(256) | bc.BC_LOOP_GRAPH, bc.BC_PATH_PLAIN):
+        a, _ = bc.bc_sources(h, g.n, src, fl)
+        b, _ = bc.bc_sources(h, g.n, src, fl)
+        assert np.array_equal(a, b), fl
+    d0 = bc.bc_tile_sssp(h, g.n, src[:40], TILED | bc.BC_TILE(64))
+    d1 = bc.bc_tile_sssp(h, g.n, src[:40], TILED | bc.BC_TILE(64))
+    assert all(np.array_equal(x, y) for x, y in zip(d0, d1))
+    for fl in (0, bc.BC_PLAIN_GRID):
+        s0 = bc.bc_sssp(h, g.n, int(src[0]), fl)
+        s1 = bc.bc_sssp(h, g.n, int(src[0]), fl)
+        assert all(np.array_equal(x, y) for x, y in zip(s0, s1))
+    bc.bc_destroy(h)
+    gh = hub_chunk_graph()
+    h = upload(ctx, gh)
+    src = np.arange(0, gh.n, 53, dtype=np.int32)
+    a, _ = bc.bc_sources(h, gh.n, src, TILED | bc.BC_TILE(64))
+    b, _ = bc.bc_sources(h, gh.n, src, TILED | bc.BC_TILE(64))
+    assert np.array_equal(a, b)
     bc.bc_destroy(h)
