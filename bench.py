@@ -188,18 +188,28 @@ def algorithmic_bytes(stats: dict, tile_width: int) -> float:
     return (8.0 * ar + 16.0 * nr) / tile_width + 68.0 * nr
 
 
+def code_sha1(path: str) -> str:
+    """sha1 of a C/CUDA source with its comments and blank lines removed: it changes when
+    the code changes, not when a comment does."""
+    import hashlib
+    import re
+    with open(path) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    lines = [ln.rstrip() for ln in text.splitlines()]
+    return hashlib.sha1("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()
+
+
 def ncu_traffic(T: int, tiles_bytes: float):
     """DRAM bytes (read + write) per launch of the tile kernel from the committed ncu
-    summary, if it was taken on the current kernel source and this tile width."""
-    import hashlib
+    summary, if it was taken on the current kernel code and this tile width."""
     path = os.path.join(ROOT, "profiles", "tile_rmat20_dram.json")
     src = os.path.join(ROOT, "paper_1602_00963_gb300", "csrc", "bc_tile.cu")
     try:
         with open(path) as f:
             j = json.load(f)
-        with open(src, "rb") as f:
-            digest = hashlib.sha1(f.read()).hexdigest()
-        if j.get("kernel_source_sha1") != digest or int(j.get("tile_width", 0)) != T:
+        if j.get("kernel_code_sha1") != code_sha1(src) or int(j.get("tile_width", 0)) != T:
             return None
         return float(j["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):

@@ -18,8 +18,9 @@
 // 2^e; a warp per vertex w of level d sums its successors' r, rescaled to w's exponent, in
 // float-float arithmetic (lanes in edge order, then a fixed-order warp reduction); then
 // delta = m * sum, r[w] = (1 + omega) / m + sum, and the CTA's BC partial of w grows by
-// (omega[s] + 1) * delta.  A second kernel sums the partials in CTA order, so the result is
-// deterministic.
+// (omega[s] + 1) * delta.  A second kernel sums the partials in CTA order, so the result
+// repeats bit for bit unless a level holds more vertices above the per-thread degree than
+// the shared list takes (then which of them a single thread handles depends on timing).
 #include <algorithm>
 #include <climits>
 #include <cstring>

@@ -149,9 +149,9 @@ bc_status prune_build(Ctx *ctx, Graph *g, cudaStream_t st) {
     prune_free(ctx, &p);
     return cuda_fail(e, "1-degree preprocessing");
   }
-  // Sort the source list so that runs are reproducible (the compaction order depends
-  // on warp scheduling); a plain device radix pass is not needed for correctness, but
-  // a fixed order makes the per-vertex BC sums bit-reproducible across calls.
+  // Sort the source list (the compaction order depends on warp scheduling): not needed
+  // for correctness, but every call then gives the same sources to the same tiles and
+  // CTAs.
   p.nsrc = h;
   std::vector<int32_t> hs(h);
   if (h) {

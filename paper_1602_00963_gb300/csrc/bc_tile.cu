@@ -32,8 +32,11 @@
 // source lanes.  Levels whose entries average at most two sources and 16 edges (high-
 // diameter graphs) run one entry per lane instead.  Vertices of degree >= kHub are
 // processed by whole CTAs (forward) or as 4096-edge items spread over CTAs (backward).
-// Warp-level work is numbered across CTAs first.  All sums run in a fixed order, so the
-// tile path is deterministic.
+// Warp-level work is numbered across CTAs first.  σ, depth and the masks are exact.  The
+// float-float r sums of an entry walked warp-wide take each 32-edge step's two-source hits
+// before its row gathers, and where the steps fall depends on the ranges the warps claim
+// at run time, so r and BC can differ in the last bits from one run to the next; the
+// lane-per-entry mode and the hub items sum in a fixed order.
 //
 // sigma beyond 2^64: a tile first runs with r computed from sigma mod 2^64; if any count
 // overflowed, the tile is rerun (before any BC update) in extended mode, where each
@@ -804,7 +807,7 @@ __device__ bool pull_hub_cta(const TK &p, int w, int level, bool leaf,
 // per round, their loads in flight together), keeping the sums of two sources at a time in
 // registers (one pass per pair).  Entries with more than kLaneSrc sources or kLaneDeg
 // edges fall back to the warp-wide path, one at a time; hubs stay with whole CTAs.  Each
-// (entry, source) sum runs in edge order, so the results stay deterministic.
+// (entry, source) sum runs in edge order.
 constexpr int kLaneDeg = 64;
 constexpr int kLaneSrc = 8;  // sources per lane-mode entry (in passes of two)
 

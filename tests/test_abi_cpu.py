@@ -62,3 +62,16 @@ def test_bench_deg2_triple_count_matches_the_selection_rule():
     for g in [gg.cycle_graph(17), gg.subdivide_edges(gg.grid2d(12, 12, seed=1, delete_frac=0.1), 0.4, 2),
               gg.random_tree(60, 4)]:
         assert bench.deg2_triples(g) == len(deg2.select_triples(g))
+
+
+def test_code_hash_ignores_comments_only(tmp_path):
+    """bench.py ties the committed ncu traffic figure to the tile kernel's code: editing a
+    comment keeps the hash, editing code changes it."""
+    import bench
+    src = os.path.join(ROOT, "paper_1602_00963_gb300", "csrc", "bc_tile.cu")
+    text = open(src).read()
+    a = tmp_path / "a.cu"
+    a.write_text(text.replace("// Warp-level work is numbered", "// Warp work is numbered"))
+    b = tmp_path / "b.cu"
+    b.write_text(text.replace("constexpr int kHub = 2048;", "constexpr int kHub = 2049;"))
+    assert bench.code_sha1(str(a)) == bench.code_sha1(src) != bench.code_sha1(str(b))
