@@ -5,6 +5,7 @@
 #include <string>
 
 #include "bc_internal.h"
+#include "bc_scan.cuh"
 
 namespace bcl {
 
@@ -112,17 +113,18 @@ __global__ void k_degree_stats(int32_t n, const int32_t *rp, unsigned long long 
 
 // Sources of a full run: every vertex with at least one edge (an isolated source
 // reaches nothing and contributes nothing).
-__global__ void k_nonisolated_list(int32_t n, const int32_t *rp, int32_t *out, int *count) {
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += stride) {
-    int64_t v = base + threadIdx.x;
-    bool keep = v < n && rp[v + 1] > rp[v];
-    unsigned m = __ballot_sync(BC_FULL, keep);
-    int pos = 0;
-    if ((threadIdx.x & 31) == 0 && m) pos = atomicAdd(count, __popc(m));
-    pos = __shfl_sync(BC_FULL, pos, 0);
-    if (keep) out[pos + __popc(m & lanemask_lt())] = (int32_t)v;
-  }
+// flag[v] = 1 for a vertex with an edge (v < n), flag[n] = 0
+__global__ void k_nonisolated_flags(int32_t n, const int32_t *rp, int32_t *flag) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v <= n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    flag[v] = (v < n && rp[v + 1] > rp[v]) ? 1 : 0;
+}
+
+// out[pos[v]] = v for every vertex with an edge: the list in increasing vertex order
+__global__ void k_nonisolated_scatter(int32_t n, const int32_t *rp, const int32_t *pos, int32_t *out) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    if (rp[v + 1] > rp[v]) out[pos[v]] = (int32_t)v;
 }
 
 __global__ void k_check_sources(int32_t n, const int32_t *src, int32_t k, int *err) {
@@ -347,21 +349,36 @@ bc_status bc_graph_create(bc_ctx *ctx, int32_t n, const int32_t *row_ptr,
   return BC_OK;
 }
 
-// All non-isolated vertices of dg as a device source list (cached on the graph for
-// the full graph; built into `buf` otherwise).
+// All non-isolated vertices of dg, in increasing order, as a device source list built
+// into `buf` (an ordered compaction: flags, exclusive scan, scatter), so every call gives
+// the same sources to the same tiles and CTAs.
 static bc_status full_source_list(Graph *g, const DeviceGraph *dg, int32_t **list, int32_t *count,
                                   DevBuf &buf, cudaStream_t st) {
   Ctx *c = g->ctx;
-  bc_status s = buf.get(c, ((size_t)dg->n + 1) * 4);
+  const int64_t n1 = (int64_t)dg->n + 1;
+  bc_status s = buf.get(c, (size_t)n1 * 4);
   if (s) return s;
-  int *d_cnt = nullptr;
-  BC_CUDA_TRY(cudaMalloc(&d_cnt, 4));
-  cudaMemsetAsync(d_cnt, 0, 4, st);
-  k_nonisolated_list<<<grid_for(dg->n, c->num_sms), 256, 0, st>>>(dg->n, dg->rp, (int32_t *)buf.p, d_cnt);
+  int32_t *flag = nullptr, *pos = nullptr;
+  void *scratch = nullptr;
+  cudaError_t e = cudaMalloc(&flag, (size_t)n1 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&pos, (size_t)n1 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&scratch, scan_scratch_bytes(n1));
+  const int nb = grid_for(dg->n, c->num_sms);
+  if (e == cudaSuccess) {
+    k_nonisolated_flags<<<nb, 256, 0, st>>>(dg->n, dg->rp, flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = scan_exclusive_i32(flag, pos, n1, scratch, st);
+  if (e == cudaSuccess) {
+    k_nonisolated_scatter<<<nb, 256, 0, st>>>(dg->n, dg->rp, pos, (int32_t *)buf.p);
+    e = cudaGetLastError();
+  }
   int h = 0;
-  cudaMemcpyAsync(&h, d_cnt, 4, cudaMemcpyDeviceToHost, st);
-  cudaError_t e = cudaStreamSynchronize(st);
-  cudaFree(d_cnt);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, pos + dg->n, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (flag) cudaFree(flag);
+  if (pos) cudaFree(pos);
+  if (scratch) cudaFree(scratch);
   if (e != cudaSuccess) return cuda_fail(e, "source list");
   *list = (int32_t *)buf.p;
   *count = h;
