@@ -75,3 +75,37 @@ def test_code_hash_ignores_comments_only(tmp_path):
     b = tmp_path / "b.cu"
     b.write_text(text.replace("constexpr int kHub = 2048;", "constexpr int kHub = 2049;"))
     assert bench.code_sha1(str(a)) == bench.code_sha1(src) != bench.code_sha1(str(b))
+
+
+def test_header_compiles_as_c_and_links(lib, tmp_path):
+    """include/bc.h is plain C (C11, warnings as errors) and a C program links against
+    libbc.so and calls it; without a GPU only calls that need no device are made."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include "bc.h"
+#include <stdio.h>
+#include <string.h>
+int main(void) {
+  char msg[256];
+  const char *v = bc_version();
+  if (!v || !strstr(v, "sm_103a")) return 2;
+  if (bc_destroy(NULL) != BC_EINVAL) return 3;
+  bc_last_error(msg, sizeof msg);
+  if (!strstr(msg, "bc_destroy")) return 4;
+  if (bc_sources_noalloc(BC_NOALLOC_MAX_N + 1, NULL, NULL, 0, NULL, 0, NULL, NULL) != BC_EINVAL) return 5;
+  printf("%s\n", v);
+  return 0;
+}
+''')
+    libdir = os.path.dirname(lib._name)
+    exe = tmp_path / "abi"
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                           "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lbc",
+                           "-o", str(exe)])
+    env = dict(os.environ, LD_LIBRARY_PATH=libdir + os.pathsep + os.environ.get("LD_LIBRARY_PATH", ""))
+    r = subprocess.run([str(exe)], env=env, capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
