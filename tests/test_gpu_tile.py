@@ -218,7 +218,9 @@ def test_repeat_runs(ctx):
     """Repeated calls: depth, sigma and the overflow flags are identical on every path.  The
     tile path's float-float r sums take each 32-edge step's two-source hits before its row
     gathers and the steps fall where the warps' run-time range claims put them, so BC may
-    move in the last bits (bounded here by 1e-13 relative); the per-CTA kernel repeats bit
+    move in the last bits: a reordered float-float sum of N terms moves by at most about
+    N * 2^-48 relative, and entries walked warp-wide have fewer than 2048 edges (hubs go
+    through fixed-order chunks), hence the bound 1e-11; the per-CTA kernel repeats bit
     for bit while no level holds more vertices above its per-thread degree (32) than its
     shared list takes, which graphs of degree <= 32 guarantee."""
     g = gg.rmat(12, 16, 1)
@@ -227,7 +229,7 @@ def test_repeat_runs(ctx):
     for fl in (TILED | bc.BC_TILE(64), TILED | bc.BC_TILE(256) | bc.BC_LOOP_GRAPH):
         a, _ = bc.bc_sources(h, g.n, src, fl)
         b, _ = bc.bc_sources(h, g.n, src, fl)
-        assert np.all(np.abs(a - b) <= 1e-13 * np.maximum(np.abs(a), 1.0)), fl
+        assert np.all(np.abs(a - b) <= 1e-11 * np.maximum(np.abs(a), 1.0)), fl
     d0 = bc.bc_tile_sssp(h, g.n, src[:40], TILED | bc.BC_TILE(64))
     d1 = bc.bc_tile_sssp(h, g.n, src[:40], TILED | bc.BC_TILE(64))
     assert all(np.array_equal(x, y) for x, y in zip(d0, d1))
@@ -241,7 +243,7 @@ def test_repeat_runs(ctx):
     src = np.arange(0, gh.n, 53, dtype=np.int32)
     a, _ = bc.bc_sources(h, gh.n, src, TILED | bc.BC_TILE(64))
     b, _ = bc.bc_sources(h, gh.n, src, TILED | bc.BC_TILE(64))
-    assert np.all(np.abs(a - b) <= 1e-13 * np.maximum(np.abs(a), 1.0))
+    assert np.all(np.abs(a - b) <= 1e-11 * np.maximum(np.abs(a), 1.0))
     bc.bc_destroy(h)
     for gc in (gg.grid2d(48, 48), gg.gnm(3000, 9000, 4)):  # sigma past 2^64; random sparse
         assert gc.degrees().max() <= 32
