@@ -7,11 +7,16 @@ drawn uniformly from the largest component (seed 4); tiles of 32..256 sources pe
 launch, tile width chosen by the autotuner.  One step = one bc_sources call over the
 4096 sources (forward sigma counting + backward dependency sweep + BC accumulation).
 
-Also reported beside the headline: the per-source path on the same graph and GPU (a
+Also reported beside the headline: the same step end to end through the C ABI with host
+buffers (e2e), the tile kernel's roofline, the per-source path on the same graph and GPU (a
 sample of its sources), each tile width, the all-sources runs of the R-MAT scale-12
-graph, and the oracle on the host cores (cpu_baseline).
+graph, the leaf-rich graph pruned vs unpruned, the 1024 x 1024 grid's level-loop modes,
+the serving sweep (p50/p99 latency per arrival rate), and the oracle on the host cores
+(cpu_baseline).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       python bench.py --study deg1|deg2|scan     (one study, one JSON line)
+       python bench.py --profile-case SPEC         (one small call for a profiler)
 Multi-GPU (torchrun): each rank runs its own replica on its own GPU with its own 4096
 seeded sources (weak scaling, no collective: BC is additive over sources).
 """
