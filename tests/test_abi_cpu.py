@@ -97,6 +97,13 @@ int main(void) {
   bc_last_error(msg, sizeof msg);
   if (!strstr(msg, "bc_destroy")) return 4;
   if (bc_sources_noalloc(BC_NOALLOC_MAX_N + 1, NULL, NULL, 0, NULL, 0, NULL, NULL) != BC_EINVAL) return 5;
+  /* size limits are checked before any device work: n in [1, max], nnz in [0, 2^31) */
+  int32_t rp[2] = {0, 0}, src[1] = {0};
+  double out[1];
+  if (bc_sources_noalloc(0, rp, rp, 0, src, 1, out, NULL) != BC_EINVAL) return 6;
+  if (bc_sources_noalloc(1, rp, rp, (int64_t)1 << 31, src, 1, out, NULL) != BC_EINVAL) return 7;
+  if (bc_sources_noalloc(1, rp, rp, -1, src, 1, out, NULL) != BC_EINVAL) return 8;
+  if (bc_sources_noalloc(1, rp, rp, 0, src, -1, out, NULL) != BC_EINVAL) return 9;
   printf("%s\n", v);
   return 0;
 }

@@ -165,6 +165,13 @@ def test_invalid_inputs(ctx):
         bc.bc_sources(h, g.n, np.array([1], np.int32), PLAIN | bc.BC_PRUNE_DEG1)
     assert e.value.status == bc.BC_EINVAL
     bc.bc_destroy(h)
+    # size limits of the int32 CSR, checked before any device work: nnz in [0, 2^31), even
+    # (each edge stored twice), n >= 1
+    rp, ci = np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32)
+    for n, nnz in ((2, 2**31), (2, -2), (2, 3), (0, 0)):
+        with pytest.raises(bc.BCError) as e:
+            bc.bc_graph_create(ctx, n, rp, ci, nnz, 0)
+        assert e.value.status == bc.BC_EINVAL, (n, nnz)
 
 
 def test_wait_limit_timeout_then_recovery(ctx):
