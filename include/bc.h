@@ -219,16 +219,20 @@ const char *bc_version(void);
  * hard device-memory quota.
  * Computes the same as bc_sources(..., BC_PATH_PLAIN | BC_DEVICE_PTRS, ...): the sum
  * over the multiset src[k] of delta_s, on the graph given by row_ptr[n+1] / col_idx[nnz]
- * (a symmetric CSR as for bc_graph_create; not validated here).  Every pointer is a
- * device pointer owned by the caller; bc_out[n] is overwritten.  Working storage is one
- * static device array of about 3.7 MB, sized for BC_NOALLOC_MAX_N vertices, that every
- * GPU loading the library holds until the process exits; the call allocates nothing,
- * clears that array at its start and returns when the result is complete.  Calls in one
- * process share the array and are serialised (one runs at a time, to completion); each
- * process has its own copy of it, so calls in different processes never share it.  The
- * first call on a device looks
- * up the array's device address with that device current: make it before any stream
- * capture.  n > BC_NOALLOC_MAX_N returns BC_EINVAL. */
+ * (a symmetric CSR as for bc_graph_create; its structure is not validated here).  Every
+ * pointer is a device pointer owned by the caller; bc_out[n] is overwritten (zeros for
+ * k = 0).  Working storage is one static device array of about 3.7 MB, sized for
+ * BC_NOALLOC_MAX_N vertices, that every GPU loading the library holds until the process
+ * exits; the CUDA runtime places it on a device when it loads the library's device code
+ * there (with lazy module loading: at the latest during the first call on that device),
+ * and no call allocates anything.  The call clears that array at its start, checks every
+ * source id on the device, and synchronises cuda_stream twice (after the check and after
+ * the traversal): it returns when the result is complete.  Calls in one process share the
+ * array and are serialised (one runs at a time, to completion); each process has its own
+ * copy of it, so calls in different processes never share it.  The first call on a device
+ * looks up the array's device address with that device current: make it before any stream
+ * capture.  BC_EINVAL: n outside [1, BC_NOALLOC_MAX_N], nnz odd or outside [0, 2^31), k < 0,
+ * a NULL pointer, or a source id outside [0, n). */
 #define BC_NOALLOC_MAX_N 65536
 bc_status bc_sources_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                              int64_t nnz, const int32_t *src, int32_t k, double *bc_out,

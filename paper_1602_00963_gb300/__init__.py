@@ -303,9 +303,19 @@ def bc_sources_noalloc(n: int, row_ptr, col_idx, src, bc_out, stream=None):
     """Allocation-free variant for callers that cannot allocate device memory: all
     arguments are CUDA tensors the caller owns (int32 CSR, int32 sources, float64 output);
     the library works in a static device scratch array (n <= BC_NOALLOC_MAX_N)."""
-    for t in (row_ptr, col_idx, src, bc_out):
+    import torch
+    for name, t, dt in (("row_ptr", row_ptr, torch.int32), ("col_idx", col_idx, torch.int32),
+                        ("src", src, torch.int32), ("bc_out", bc_out, torch.float64)):
         if not _is_cuda(t):
             raise ValueError("bc_sources_noalloc takes CUDA tensors only")
+        if t.dtype != dt:
+            raise ValueError(f"bc_sources_noalloc: {name} must be {dt}, not {t.dtype}")
+        if t.device != row_ptr.device:
+            raise ValueError("bc_sources_noalloc: all tensors must be on one device")
+    if row_ptr.numel() != int(n) + 1:
+        raise ValueError(f"bc_sources_noalloc: row_ptr has {row_ptr.numel()} entries, not n + 1 = {int(n) + 1}")
+    if bc_out.numel() < int(n):
+        raise ValueError(f"bc_sources_noalloc: bc_out has {bc_out.numel()} entries, fewer than n = {int(n)}")
     _check(load().bc_sources_noalloc(int(n), _ptr(row_ptr), _ptr(col_idx), int(col_idx.numel()),
                                      _ptr(src), int(src.numel()), _ptr(bc_out),
                                      ctypes.c_void_p(stream) if stream else None))

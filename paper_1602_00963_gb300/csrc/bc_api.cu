@@ -323,14 +323,15 @@ bc_status bc_graph_create(bc_ctx *ctx, int32_t n, const int32_t *row_ptr,
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(hs, d_scr, 16, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (d_scr) cudaFree(d_scr);
   if (e != cudaSuccess) {
+    if (d_scr) cudaFree(d_scr);
     c->mem.release(g->g.rp, rb);
     c->mem.release(g->g.ci, cb);
     delete g;
     return cuda_fail(e, "bc_graph_create: upload");
   }
   if (hs[0]) {
+    cudaFree(d_scr);
     c->mem.release(g->g.rp, rb);
     c->mem.release(g->g.ci, cb);
     delete g;
@@ -341,6 +342,7 @@ bc_status bc_graph_create(bc_ctx *ctx, int32_t n, const int32_t *row_ptr,
   }
   g->max_degree = hs[1];
   g->n_nonisolated = (int64_t)(*(unsigned long long *)(hs + 2));
+  g->d_chk = d_scr;  // kept for the source checks of later calls
   {
     std::lock_guard<std::mutex> lk(c->mu);
     c->graphs.push_back(g);
@@ -519,15 +521,13 @@ bc_status bc_sources(bc_graph *graph, const int32_t *src, int32_t k, uint32_t fl
       d_src = (const int32_t *)sbuf.p;
     }
   } else if (k) {
-    int *d_err = nullptr;
-    BC_CUDA_TRY(cudaMalloc(&d_err, 4));
-    cudaMemsetAsync(d_err, 0, 4, st);
-    k_check_sources<<<grid_for(k, c->num_sms), 256, 0, st>>>(n, src, k, d_err);
+    // the graph's check word (calls on one graph are serialised by g->mu)
+    BC_CUDA_TRY(cudaMemsetAsync(g->d_chk, 0, 4, st));
+    k_check_sources<<<grid_for(k, c->num_sms), 256, 0, st>>>(n, src, k, g->d_chk);
+    BC_CUDA_TRY(cudaGetLastError());
     int h = 0;
-    cudaMemcpyAsync(&h, d_err, 4, cudaMemcpyDeviceToHost, st);
-    cudaError_t e = cudaStreamSynchronize(st);
-    cudaFree(d_err);
-    if (e != cudaSuccess) return cuda_fail(e, "bc_sources: source check");
+    BC_CUDA_TRY(cudaMemcpyAsync(&h, g->d_chk, 4, cudaMemcpyDeviceToHost, st));
+    BC_CUDA_TRY(cudaStreamSynchronize(st));
     if (h) return fail(BC_EINVAL, "bc_sources: source id out of range");
   }
   BC_CUDA_TRY(cudaMemsetAsync(d_bc, 0, (size_t)n * 8, st));
@@ -696,6 +696,7 @@ static void graph_free(Graph *g) {
   }
   c->mem.release(g->g.rp, ((size_t)g->g.n + 1) * 4);
   c->mem.release(g->g.ci, (size_t)g->g.nnz * 4);
+  if (g->d_chk) cudaFree(g->d_chk);
   g->magic = 0;
   delete g;
 }

@@ -120,6 +120,7 @@ struct Graph {
   TileWS *tile = nullptr;  // tile-path workspace (bc_tile.cu)
   CtaWS *cta = nullptr;    // per-source path on small graphs (bc_cta.cu)
   std::vector<int32_t> h_deg_nonisolated;  // host copy for sampled requests
+  int *d_chk = nullptr;    // device words for argument checks (16 bytes, graph's lifetime)
 };
 
 struct Server;  // bc_serve.cu

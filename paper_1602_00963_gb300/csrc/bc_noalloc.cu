@@ -10,16 +10,23 @@
 // else lives in the static scratch below.
 //
 // Limits and rules:
-//   * n <= BC_NOALLOC_MAX_N; larger graphs are rejected with BC_EINVAL.
+//   * n <= BC_NOALLOC_MAX_N; larger graphs are rejected with BC_EINVAL, and so are an odd
+//     nnz and any source id outside [0, n) (checked on the device before the traversal;
+//     the CSR itself is not validated).
 //   * The scratch (about 3.7 MB) is part of the library image: every GPU on which the
 //     library is loaded holds it until the process exits.
 //   * All calls of a process share the one array.  The entry point clears what must start
 //     cleared at the beginning of every call and holds a lock until the call's work is
 //     complete, so one call runs at a time.  Each process gets its own copy of the array
 //     (a module global lives in the process's own CUDA context).
+//   * The CUDA runtime places the array on a device when it loads the library's device
+//     code there (with lazy loading: at the latest during the first call on that device);
+//     the calls themselves allocate nothing.
 //   * The first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress) with that device current; make that first call before any
 //     stream capture.
+//   * A call waits for its own work: it synchronises the given stream (after the source
+//     check and after the traversal) before it returns.
 #include <cstring>
 #include <mutex>
 
@@ -49,7 +56,8 @@ constexpr size_t o_ovf = o_xe + al256(kN2 * 4);
 constexpr size_t o_vis = o_ovf + al256(kNW * 4);
 constexpr size_t o_front = o_vis + al256(kNW * 4);
 constexpr size_t o_ctl = o_front + al256(kNW * 4);
-constexpr size_t kScratchBytes = o_ctl + al256(sizeof(PlainCtl));
+constexpr size_t o_chk = o_ctl + al256(sizeof(PlainCtl));  // source-range check word
+constexpr size_t kScratchBytes = o_chk + 256;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -79,6 +87,14 @@ __global__ void k_noalloc_clear(unsigned char *base, int n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sizeof(PlainCtl) / 4;
        i += (size_t)gridDim.x * blockDim.x)
     ctl[i] = 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *(int *)(base + o_chk) = 0;
+}
+
+// Sets the check word when a source id lies outside [0, n): the per-source kernel indexes
+// its state arrays with the ids, so none may run past them.
+__global__ void k_noalloc_check(const int32_t *src, int32_t k, int32_t n, unsigned char *base) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
+    if (src[i] < 0 || src[i] >= n) atomicOr((int *)(base + o_chk), 1);
 }
 
 std::mutex g_mu;
@@ -97,6 +113,7 @@ extern "C" bc_status bc_sources_noalloc(int32_t n, const int32_t *row_ptr, const
                                "] (the static scratch is sized for that many vertices)");
   if (nnz < 0 || nnz >= ((int64_t)1 << 31))
     return fail(BC_EINVAL, "bc_sources_noalloc: nnz must be in [0, 2^31)");
+  if (nnz % 2) return fail(BC_EINVAL, "bc_sources_noalloc: a symmetric CSR has an even nnz");
   if (!row_ptr || (nnz > 0 && !col_idx) || !bc_out || k < 0 || (k > 0 && !src))
     return fail(BC_EINVAL, "bc_sources_noalloc: NULL argument or k < 0");
   std::lock_guard<std::mutex> lk(g_mu);
@@ -115,6 +132,14 @@ extern "C" bc_status bc_sources_noalloc(int32_t n, const int32_t *row_ptr, const
   BC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   k_noalloc_clear<<<sms * 4, 256, 0, st>>>(base, n);
   BC_CUDA_TRY(cudaGetLastError());
+  if (k > 0) {
+    k_noalloc_check<<<sms, 256, 0, st>>>(src, k, n, base);
+    BC_CUDA_TRY(cudaGetLastError());
+    int bad = 0;
+    BC_CUDA_TRY(cudaMemcpyAsync(&bad, base + o_chk, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (bad) return fail(BC_EINVAL, "bc_sources_noalloc: source id out of range [0, n)");
+  }
   BC_CUDA_TRY(cudaMemsetAsync(bc_out, 0, (size_t)n * sizeof(double), st));
   PlainWS ws;
   ws.n = n;

@@ -28,6 +28,7 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "bc_internal.h"
 
@@ -646,7 +647,27 @@ __global__ void __launch_bounds__(kThreads, 1) plain_kernel(PK p) {
   }
 }
 
-int g_blocks_per_sm = -1;
+// The dynamic shared-memory size of plain_kernel is an attribute of the function on one
+// device: it is set on each device before that device's first launch.
+std::mutex g_setup_mu;
+bool g_setup_done[128];
+
+bc_status plain_setup(int *blocks_per_sm) {
+  int dev = 0;
+  BC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return fail(BC_EINVAL, "per-source kernel: device index out of range");
+  std::lock_guard<std::mutex> lk(g_setup_mu);
+  if (!g_setup_done[dev]) {
+    BC_CUDA_TRY(cudaFuncSetAttribute(plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSmemBytes));
+    int b = 0;
+    BC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, plain_kernel, kThreads, kSmemBytes));
+    if (b < 1) return fail(BC_ECUDA, "per-source kernel does not fit on an SM");
+    g_setup_done[dev] = true;
+  }
+  *blocks_per_sm = 1;  // one CTA of 1024 threads per SM
+  return BC_OK;
+}
 
 }  // namespace
 
@@ -713,14 +734,9 @@ bc_status plain_run_view(const PlainWS &ws, const PlainArgs &a, int num_sms, uin
                          cudaStream_t st, int *dev_err) {
   *dev_err = 0;
   if (a.nsrc <= 0) return BC_OK;
-  if (g_blocks_per_sm < 0) {
-    BC_CUDA_TRY(cudaFuncSetAttribute(plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSmemBytes));
-    int b = 0;
-    BC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, plain_kernel, kThreads, kSmemBytes));
-    if (b < 1) return fail(BC_ECUDA, "per-source kernel does not fit on an SM");
-    g_blocks_per_sm = 1;
-  }
+  int bps = 0;
+  bc_status s = plain_setup(&bps);
+  if (s) return s;
   PK p;
   memset(&p, 0, sizeof(p));
   p.n = a.g->n;
@@ -751,7 +767,7 @@ bc_status plain_run_view(const PlainWS &ws, const PlainArgs &a, int num_sms, uin
   p.beta = a.beta;
   p.limit_ns = limit_ns;
   void *args[] = {&p};
-  cudaError_t le = cudaLaunchCooperativeKernel((void *)plain_kernel, dim3(num_sms * g_blocks_per_sm),
+  cudaError_t le = cudaLaunchCooperativeKernel((void *)plain_kernel, dim3(num_sms * bps),
                                                dim3(kThreads), args, kSmemBytes, st);
   if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(plain_kernel)");
   int err = 0;
@@ -763,13 +779,10 @@ bc_status plain_run_view(const PlainWS &ws, const PlainArgs &a, int num_sms, uin
 
 bc_status plain_run(Ctx *ctx, PlainWS *ws, const PlainArgs &a, cudaStream_t st, bc_stats *acc) {
   if (a.nsrc <= 0) return BC_OK;
-  if (g_blocks_per_sm < 0) {
-    BC_CUDA_TRY(cudaFuncSetAttribute(plain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSmemBytes));
-    int b = 0;
-    BC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, plain_kernel, kThreads, kSmemBytes));
-    if (b < 1) return fail(BC_ECUDA, "per-source kernel does not fit on an SM");
-    g_blocks_per_sm = 1;
+  int bps = 0;
+  {
+    const bc_status s = plain_setup(&bps);
+    if (s) return s;
   }
   PK p;
   p.n = a.g->n;
@@ -805,7 +818,7 @@ bc_status plain_run(Ctx *ctx, PlainWS *ws, const PlainArgs &a, cudaStream_t st, 
   p.trace = nullptr;
   p.trace_cap = 0;
   p.no_cd_reuse = a.no_cd_reuse ? 1 : 0;
-  if (a.no_cd_reuse && ctx->num_sms * g_blocks_per_sm > kPlainScanBlocks)
+  if (a.no_cd_reuse && ctx->num_sms * bps > kPlainScanBlocks)
     return fail(BC_EINVAL, "BC_NO_CD_REUSE: more CTAs than the rescan supports");
   static const char *trace_file = getenv("BC_TRACE_FILE");
   if (trace_file) {
@@ -816,7 +829,7 @@ bc_status plain_run(Ctx *ctx, PlainWS *ws, const PlainArgs &a, cudaStream_t st, 
       p.trace_cap = 0;
     }
   }
-  dim3 grid(ctx->num_sms * g_blocks_per_sm), block(kThreads);
+  dim3 grid(ctx->num_sms * bps), block(kThreads);
   void *args[] = {&p};
   BC_CUDA_TRY(cudaMemsetAsync(ws->ctl, 0, sizeof(PlainCtl), st));
   cudaEvent_t e0, e1;

@@ -49,6 +49,7 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "bc_ff.cuh"
@@ -2066,14 +2067,21 @@ KPtrs kptrs(int G, bool ext) {
   }
 }
 
-bool g_attr_done[2][9];
+// The dynamic shared-memory size is an attribute of a function on one device: set per
+// device before that device's first launch of the variant.
+std::mutex g_attr_mu;
+bool g_attr_done[128][2][9];
 
 bc_status set_attrs(int G, bool ext) {
-  if (g_attr_done[ext][G]) return BC_OK;
+  int dev = 0;
+  BC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return fail(BC_EINVAL, "tile path: device index out of range");
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (g_attr_done[dev][ext][G]) return BC_OK;
   const KPtrs k = kptrs(G, ext);
   for (void *f : {k.persistent, k.pull, k.blevel})
     BC_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTile));
-  g_attr_done[ext][G] = true;
+  g_attr_done[dev][ext][G] = true;
   return BC_OK;
 }
 

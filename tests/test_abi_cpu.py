@@ -104,6 +104,7 @@ int main(void) {
   if (bc_sources_noalloc(1, rp, rp, (int64_t)1 << 31, src, 1, out, NULL) != BC_EINVAL) return 7;
   if (bc_sources_noalloc(1, rp, rp, -1, src, 1, out, NULL) != BC_EINVAL) return 8;
   if (bc_sources_noalloc(1, rp, rp, 0, src, -1, out, NULL) != BC_EINVAL) return 9;
+  if (bc_sources_noalloc(1, rp, rp, 3, src, 1, out, NULL) != BC_EINVAL) return 10; /* odd nnz */
   printf("%s\n", v);
   return 0;
 }
