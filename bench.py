@@ -17,8 +17,9 @@ the serving sweep (p50/p99 latency per arrival rate), and the oracle on the host
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
        python bench.py --study deg1|deg2|scan     (one study, one JSON line)
        python bench.py --profile-case SPEC         (one small call for a profiler)
-Multi-GPU (torchrun): each rank runs its own replica on its own GPU with its own 4096
-seeded sources (weak scaling, no collective: BC is additive over sources).
+Multi-GPU (torchrun): each rank runs the graph on its own GPU with its own 4096 seeded
+sources (weak scaling) and, once per step inside the timed region, the ranks sum their BC
+vectors with one NCCL all-reduce (BC is additive over sources).
 """
 from __future__ import annotations
 
@@ -40,6 +41,10 @@ if ROOT not in sys.path:
 import graphgen as gg  # noqa: E402
 
 METRIC = "BC GTEPS (sources·m/s) batched vs per-source on 1 GB300; serving p50/p99 latency"
+# what the path computes in: path counts as 64-bit integers (modulo 2^64, extended range past
+# it), dependency sums as float-float pairs (two f32, about 48 significant bits), the BC
+# accumulation in f64
+DTYPE = "u64+ff32x2+f64"
 WORKLOAD = {
     "workload": "rmat-s20-ef16 batched exact BC, 4096 LCC sources",
     "graph": "R-MAT scale 20, edge factor 16, a/b/c/d .57/.19/.19/.05, seed 3",
@@ -123,6 +128,16 @@ def load_workload(nsrc: int, rank: int):
     return g, rank_sources(g, nsrc, rank)
 
 
+def reduce_bc(bc_vec, dist):
+    """Sources are split over the ranks and BC is additive over sources (Alg. 1 sums each
+    source's dependencies), so the job's BC is the sum of the ranks' vectors: one sum
+    all-reduce of the FP64 BC vector per step (the paper's coarse-grained mode with every
+    rank on its own source shard, Sec. 3.3).  No-op on one rank."""
+    if dist is not None:
+        dist.all_reduce(bc_vec)
+    return bc_vec
+
+
 def max_over_ranks(x: float, dist, device="cpu") -> float:
     """The largest of the ranks' values of x (a time): the job ends with its slowest rank."""
     if dist is None:
@@ -185,12 +200,14 @@ class ClockSampler:
 def algorithmic_bytes(stats: dict, tile_width: int) -> float:
     """Compulsory bytes of one call, per source from its reached vertices n_r and arcs a_r:
     per-source path 8 a_r + 84 n_r; a tile of width T (CSR shared by the tile)
-    (8 a_r + 16 n_r) / T + 68 n_r (each datum moved once per pass, perfect reuse)."""
+    (8 a_r + 16 n_r) / T + 68 n_r + n_r / 4 (each datum moved once per pass, perfect reuse;
+    the last term is the T-bit level masks, read and written once per vertex and level:
+    2 T / 8 bytes shared by the tile's T sources)."""
     nr = stats["reached_vertices"]
     ar = stats["reached_arcs"]
     if tile_width <= 1:
         return 8.0 * ar + 84.0 * nr
-    return (8.0 * ar + 16.0 * nr) / tile_width + 68.0 * nr
+    return (8.0 * ar + 16.0 * nr) / tile_width + 68.0 * nr + 0.25 * nr
 
 
 def code_sha1(path: str) -> str:
@@ -231,9 +248,15 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_baseline(g, src, budget_s: float = 15.0):
-    """The oracle as it stands (plain sequential Brandes, one thread per host core over
-    sources), timed on a bounded sample of the workload's sources."""
+SOFT_FLOAT = ("the oracle keeps sigma and delta in C long double: binary128 done in software "
+              "on aarch64 (Grace), 80-bit x87 on x86-64")
+
+
+def cpu_baseline(g, src, budget_s: float = 15.0, single_s: float = 8.0):
+    """The oracle as it stands (plain sequential Brandes built -O3, one thread per host core
+    over sources), timed on a bounded sample of the workload's sources; and on one core, on
+    a smaller sample (each timing a labelled sample of the same sources, as the paper's
+    totals are)."""
     import oracle
     nth = os.cpu_count() or 1
     t = time.perf_counter()
@@ -245,22 +268,31 @@ def cpu_baseline(g, src, budget_s: float = 15.0):
     t = time.perf_counter()
     oracle.bc(g, sample, nthreads=min(nth, k))
     dt = time.perf_counter() - t
+    k1 = int(max(1, min(len(src), single_s / one)))
+    t = time.perf_counter()
+    oracle.bc(g, src[:k1], nthreads=1)
+    dt1 = time.perf_counter() - t
     return {"value": k * g.m / dt / 1e9, "unit": "GTEPS", "cores": min(nth, k), "kind": "oracle",
-            "sample": f"{k} of the {len(src)} sources, one thread per core, {dt:.1f} s"}, dt / k
+            "sample": f"{k} of the {len(src)} sources, one thread per core, {dt:.1f} s; {SOFT_FLOAT}",
+            "single_core": {"value": k1 * g.m / dt1 / 1e9, "unit": "GTEPS", "cores": 1,
+                            "sample": f"{k1} of the {len(src)} sources on one core, {dt1:.1f} s"}}, dt / k
 
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
+    """The oracle on the host cores as the reference arm: the same workload, metric and
+    unit; each step runs a bounded sample of the workload's sources (about 4 s), after W
+    warm-up steps of the same sample."""
     if rank != 0:
         return
     g, src = load_workload(args.sources, 0)
-    for _ in range(args.warmup):
-        pass
-    cb, per_src = cpu_baseline(g, src, budget_s=8.0)
+    cb, per_src = cpu_baseline(g, src, budget_s=6.0, single_s=4.0)
     import oracle
     nth = os.cpu_count() or 1
-    k = max(1, int(20.0 * nth / max(per_src * nth, 1e-6)))
+    k = max(min(nth, len(src)), int(4.0 / max(per_src, 1e-6)))
     k = min(k, len(src))
+    for _ in range(args.warmup):
+        oracle.bc(g, src[:k], nthreads=min(nth, k))
     times = []
     for _ in range(args.steps):
         t = time.perf_counter()
@@ -270,10 +302,12 @@ def run_reference(args, rank, world):
     value = k * g.m / dt / 1e9
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64+f128",
             "data": "synthetic", "impl": "reference", "config": dict(WORKLOAD),
             "cpu_baseline": {"kind": "oracle", "cores": min(nth, k), "value": value,
-                             "sample": f"{k} of the {len(src)} sources per step"},
+                             "sample": f"{k} of the {len(src)} sources per step (median of "
+                                       f"{args.steps} steps); {SOFT_FLOAT}",
+                             "single_core": cb["single_core"]},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -295,23 +329,32 @@ def serving_pool():
     ]
 
 
-def serving_bench(bc, ctx, rates=(0.5, 1.0, 2.0, 4.0, 8.0), window_s=8.0, seed=100):
-    """Poisson arrivals of BC requests over the resident pool at each rate: graph uniform,
-    k = floor(exp(U(0, ln 1024))) sources, exact list or sampled with probability 1/2.
-    Reports p50 / p99 of the latency (submit -> result) and the delivered GTEPS."""
+def serving_bench(bc, ctx, per_rate=300, lam0=8.0, lam_max=1024.0, seed=100):
+    """Poisson arrivals of BC requests over the resident pool: graph uniform, k =
+    floor(exp(U(0, ln 1024))) sources, exact list or sampled with probability 1/2; per_rate
+    requests at each rate, the rate doubling from lam0 until the server saturates (p99 above
+    10 x its value at the first rate, or completions falling behind arrivals: served rate
+    below 0.8 lambda).  Reports p50 / p99 of the latency (submit -> result), the served
+    rate and the delivered GTEPS per rate; capacity_gteps is the largest delivered GTEPS
+    of the sweep (the knee)."""
     pool = serving_pool()
     handles = [bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0) for _, g in pool]
     for (_, g), h in zip(pool, handles):  # kernel choice per graph (not timed)
         if g.n > 65536:
             bc.bc_autotune(h, 64, 7)
     nonisolated = [np.flatnonzero(g.degrees() > 0).astype(np.int32) for _, g in pool]
+    for gi, (_, g) in enumerate(pool):  # workspaces set up before the sweep
+        buf = np.zeros(g.n, np.float64)
+        rid = bc.bc_stream_submit(ctx, handles[gi], buf, bc.BC_REQ_EXACT_LIST, src=nonisolated[gi][:8])
+        bc.bc_stream_poll(ctx, rid, -1)
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
-    for lam in rates:
+    lam, p99_low, saturated = lam0, None, False
+    while lam <= lam_max and not saturated:
         reqs = []
         t0 = time.perf_counter()
         t_next = 0.0
-        while t_next < window_s:
+        for _ in range(per_rate):
             t_next += rng.exponential(1.0 / lam)
             gi = int(rng.integers(0, len(pool)))
             k = int(min(1024, max(1, np.floor(np.exp(rng.uniform(0.0, np.log(1024.0)))))))
@@ -328,6 +371,7 @@ def serving_bench(bc, ctx, rates=(0.5, 1.0, 2.0, 4.0, 8.0), window_s=8.0, seed=1
                 rid = bc.bc_stream_submit(ctx, handles[gi], buf, bc.BC_REQ_SAMPLED, k=k,
                                           seed=int(rng.integers(0, 2**40)))
             reqs.append((rid, gi, k, buf))
+        offered_s = time.perf_counter() - t0
         lat, edges_done = [], 0.0
         for rid, gi, k, buf in reqs:
             st, res = bc.bc_stream_poll(ctx, rid, -1)
@@ -336,15 +380,23 @@ def serving_bench(bc, ctx, rates=(0.5, 1.0, 2.0, 4.0, 8.0), window_s=8.0, seed=1
             lat.append(res["latency_seconds"])
             edges_done += k * pool[gi][1].m
         wall = time.perf_counter() - t0
-        out.append({"lambda_per_s": lam, "requests": len(reqs),
-                    "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                    "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                    "gteps": edges_done / wall / 1e9, "wall_s": wall})
+        p50, p99 = float(np.percentile(lat, 50) * 1e3), float(np.percentile(lat, 99) * 1e3)
+        served = per_rate / wall
+        p99_low = p99 if p99_low is None else p99_low
+        saturated = p99 > 10.0 * p99_low or served < 0.8 * lam
+        out.append({"lambda_per_s": lam, "requests": len(reqs), "p50_ms": p50, "p99_ms": p99,
+                    "served_per_s": served, "gteps": edges_done / wall / 1e9, "wall_s": wall,
+                    "offered_s": offered_s, "saturated": saturated})
+        lam *= 2.0
     for h in handles:
         bc.bc_destroy(h)
-    return {"pool": [name for name, _ in pool], "window_s": window_s, "rates": out,
+    knee = max(out, key=lambda r: r["gteps"])
+    return {"pool": [name for name, _ in pool], "requests_per_rate": per_rate, "rates": out,
+            "capacity_gteps": knee["gteps"], "capacity_lambda_per_s": knee["lambda_per_s"],
+            "saturated_at_lambda_per_s": out[-1]["lambda_per_s"] if out[-1]["saturated"] else None,
             "requests": "graph uniform; k = floor(exp(U(0, ln 1024))); exact list or sampled 1:1; "
-                        "request-stream seed 100"}
+                        "request-stream seed 100; rates doubling until p99 > 10x the first rate's "
+                        "or served rate < 0.8 lambda"}
 
 
 # ------------------------------------------------------------------ side configurations
@@ -588,6 +640,7 @@ def main():
 
     for _ in range(args.warmup):
         bc.bc_sources(h, g.n, dsrc, flags, bc_out=dbc, stream=stream)
+        reduce_bc(dbc, dist)
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -597,6 +650,7 @@ def main():
         ev0.record()
         for _ in range(args.steps):
             _, st = bc.bc_sources(h, g.n, dsrc, flags, bc_out=dbc, stream=stream)
+            reduce_bc(dbc, dist)  # the job's BC over every rank's sources (N > 1)
             stats.append(st)
         ev1.record()
         barrier()
@@ -628,18 +682,20 @@ def main():
     hsrc = torch.from_numpy(src).pin_memory().numpy()
     hbc = torch.zeros(g.n, dtype=torch.float64).pin_memory().numpy()
     times = []
-    for _ in range(2):
+    for _ in range(args.steps):
         barrier()
         t = time.perf_counter()
         gh = bc.bc_graph_create(ctx, g.n, hrp, hci, g.nnz, 0)
         bc.bc_sources(gh, g.n, hsrc, flags, bc_out=hbc)
         times.append(time.perf_counter() - t)
         bc.bc_destroy(gh)
-    e_dt = max_over_ranks(min(times), dist, "cuda")
+    e_dt = max_over_ranks(statistics.median(times), dist, "cuda")
     e2e = {"value": total_sources * g.m / e_dt / 1e9, "unit": "GTEPS",
            "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col_idx.nbytes + src.nbytes),
            "d2h_bytes_per_step": int(g.n * 8), "seconds_per_step": e_dt,
-           "includes": "graph upload (CSR), sources, BC download; untuned thresholds"}
+           "steps": args.steps, "statistic": "median over steps",
+           "includes": "graph upload (CSR), sources, BC download; untuned thresholds"
+                       + ("; the ranks' BC not summed (host buffers)" if world > 1 else "")}
 
     side = {}
     if not args.quick and rank == 0:
@@ -672,10 +728,11 @@ def main():
             "metric": METRIC,
             "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
             "config": dict(WORKLOAD, tile_width=T, autotuned=tune is not None,
                            l2="inputs larger than L2 (CSR 126 MB, tile state > 1 GB)",
-                           m=g.m, n=g.n),
+                           m=g.m, n=g.n, parallelism=f"sources split over {world} rank(s), "
+                           "BC summed by one all-reduce per step" if world > 1 else "1 GPU"),
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "roofline": roofline,

@@ -79,6 +79,15 @@ enum {
  * for measuring it).  The prefix values are the same, so the result differs only by the
  * order of the kernel's floating-point atomic additions. */
 #define BC_NO_CD_REUSE    (1u << 14)
+/* bc_exact / bc_sources: the result depends only on the graph, the sources, the flags and
+ * the GPU model (reading R9 of Eq. 2's sums: a fixed summation order, so repeated runs agree
+ * bit for bit).  Every path sums in a fixed order whether or not the flag is given: the tile
+ * path adds each source's terms in the order of an entry's edges, the per-CTA kernel chooses
+ * a vertex's thread or warp path by degree alone, and the grid-wide kernel adds dependency
+ * terms as 128-bit fixed-point integers.  What the flag adds: the configuration that
+ * bc_autotune cached on the graph (a choice made by timing, so it can differ from one process
+ * to the next) is not used; without a path flag the default per-source path runs. */
+#define BC_DETERMINISTIC  (1u << 15)
 /* bits 8..11: tile width selector for BC_PATH_TILED: 0 = autotuned, else 32 << (k-1) */
 #define BC_TILE_SHIFT     8
 #define BC_TILE_MASK      (0xFu << BC_TILE_SHIFT)
@@ -221,7 +230,7 @@ const char *bc_version(void);
  * over the multiset src[k] of delta_s, on the graph given by row_ptr[n+1] / col_idx[nnz]
  * (a symmetric CSR as for bc_graph_create; its structure is not validated here).  Every
  * pointer is a device pointer owned by the caller; bc_out[n] is overwritten (zeros for
- * k = 0).  Working storage is one static device array of about 3.7 MB, sized for
+ *  k = 0).  Working storage is one static device array of about 4.2 MB, sized for
  * BC_NOALLOC_MAX_N vertices, that every GPU loading the library holds until the process
  * exits; the CUDA runtime places it on a device when it loads the library's device code
  * there (with lazy module loading: at the latest during the first call on that device),

@@ -35,12 +35,13 @@ _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 
 
 def build(force: bool = False) -> str:
-    """Compile brandes.c into liboracle.so next to it (gcc, -O2, no arch flags)."""
+    """Compile brandes.c into liboracle.so next to it (gcc, -O3, no arch flags, no fast-math:
+    the floating-point operations are those of the source, in its order)."""
     with _lock:
         stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
         if force or stale:
             tmp = _LIB + f".{os.getpid()}.tmp"
-            subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
+            subprocess.check_call(["gcc", "-O3", "-std=c11", "-shared", "-fPIC", "-pthread",
                                    "-o", tmp, _SRC])
             os.replace(tmp, _LIB)
     return _LIB

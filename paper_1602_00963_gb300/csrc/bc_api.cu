@@ -181,7 +181,8 @@ bc_status run_sources(Graph *g, const int32_t *d_src, int32_t k, uint32_t flags,
   if (tsel >= 1 && tsel <= 4) T = 32 << (tsel - 1);
   float alpha = 0.5f, beta = 24.f;
   int loop_mode = (flags & BC_LOOP_LAUNCH) ? 1 : (flags & BC_LOOP_GRAPH) ? 2 : 0;
-  if (g->tune.ready) {
+  // BC_DETERMINISTIC: the autotuner's cached choice (made by timing) is not used
+  if (g->tune.ready && !(flags & BC_DETERMINISTIC)) {
     alpha = g->tune.res.alpha;
     beta = g->tune.res.beta;
     if (!tiled && !plain) {
@@ -223,7 +224,8 @@ bc_status run_sources(Graph *g, const int32_t *d_src, int32_t k, uint32_t flags,
   pa.alpha = alpha;
   pa.beta = beta;
   pa.no_cd_reuse = (flags & BC_NO_CD_REUSE) != 0;
-  const bool want_cta = (flags & BC_PLAIN_CTA) || (!(flags & BC_PATH_PLAIN) && g->tune.ready && g->tune.res.plain_cta);
+  const bool want_cta = (flags & BC_PLAIN_CTA) || (!(flags & (BC_PATH_PLAIN | BC_DETERMINISTIC)) &&
+                                                    g->tune.ready && g->tune.res.plain_cta);
   if (!(flags & BC_PLAIN_GRID) && (cta_fits(dg->n) || (want_cta && dg->n <= kCtaForcedMaxN)))
     return cta_run(ctx, g, &g->cta, pa, st, stats);
   bc_status s = plain_ensure(ctx, &g->plain, dg->n);

@@ -18,9 +18,9 @@
 // 2^e; a warp per vertex w of level d sums its successors' r, rescaled to w's exponent, in
 // float-float arithmetic (lanes in edge order, then a fixed-order warp reduction); then
 // delta = m * sum, r[w] = (1 + omega) / m + sum, and the CTA's BC partial of w grows by
-// (omega[s] + 1) * delta.  A second kernel sums the partials in CTA order, so the result
-// repeats bit for bit unless a level holds more vertices above the per-thread degree than
-// the shared list takes (then which of them a single thread handles depends on timing).
+// (omega[s] + 1) * delta.  A second kernel sums the partials in CTA order.  Every sum has a
+// fixed order (a vertex's path depends on its degree only), so the result repeats bit for
+// bit from run to run.
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -111,27 +111,29 @@ struct CtaShared {
 
 // Entries Q[i0, i1): a vertex of degree <= kCtaLaneDeg is handled by one thread (a level of
 // a sparse, high-diameter graph then keeps every thread busy), a larger one by a whole warp
-// (lanes over its edges) from a shared list; when the list is full the thread handles it.
+// (lanes over its edges) from a shared list.  The entries are taken in windows of one per
+// thread, so the list (kCtaBig >= kCtaThreads) never fills: which path handles a vertex, and
+// so the order of its floating-point sums, depends on its degree only.
+static_assert(kCtaBig >= kCtaThreads, "a window's high-degree vertices must fit the list");
 template <typename LaneF, typename WarpF>
 __device__ __forceinline__ void cta_split(const CtaK &p, const int32_t *Q, int i0, int i1, CtaShared &sh,
                                           LaneF &&lane_f, WarpF &&warp_f) {
-  for (int i = i0 + (int)threadIdx.x; i < i1; i += kCtaThreads) {
-    const int v = Q[i];
-    if (p.rp[v + 1] - p.rp[v] > kCtaLaneDeg) {
-      const int j = atomicAdd(&sh.nbig, 1);
-      if (j < kCtaBig) {
-        sh.big[j] = v;
-        continue;
-      }
+  for (int b = i0; b < i1; b += kCtaThreads) {  // uniform over the CTA
+    const int i = b + (int)threadIdx.x;
+    if (i < i1) {
+      const int v = Q[i];
+      if (p.rp[v + 1] - p.rp[v] > kCtaLaneDeg)
+        sh.big[atomicAdd(&sh.nbig, 1)] = v;
+      else
+        lane_f(v);
     }
-    lane_f(v);
+    __syncthreads();
+    const int nb = sh.nbig;
+    __syncthreads();
+    if (threadIdx.x == 0) sh.nbig = 0;
+    for (int j = (int)(threadIdx.x >> 5); j < nb; j += kCtaWarps) warp_f(sh.big[j]);
+    __syncthreads();
   }
-  __syncthreads();
-  const int nb = sh.nbig < kCtaBig ? sh.nbig : kCtaBig;
-  __syncthreads();
-  if (threadIdx.x == 0) sh.nbig = 0;
-  for (int j = (int)(threadIdx.x >> 5); j < nb; j += kCtaWarps) warp_f(sh.big[j]);
-  __syncthreads();
 }
 
 // sigma of v as m 2^e with m in [0.5, 1)

@@ -71,7 +71,7 @@ struct PlainWS {
   uint32_t *ovf = nullptr;     // [nw] overflow bits
   uint32_t *vis = nullptr;     // [nw] visited-before-this-level bits
   uint32_t *front = nullptr;   // [nw] frontier bits (bottom-up)
-  double *acc = nullptr;       // [n] successor sums of Alg. 5
+  unsigned long long *acc = nullptr;  // [2n] successor sums of Alg. 5 (64.64 fixed point)
   double *r = nullptr;         // [n] (1 + delta + omega) / sigma
   double *xm = nullptr;        // [n] extended-range sigma: mantissa
   int32_t *xe = nullptr;       // [n] extended-range sigma: exponent

@@ -13,7 +13,7 @@
 //   * n <= BC_NOALLOC_MAX_N; larger graphs are rejected with BC_EINVAL, and so are an odd
 //     nnz and any source id outside [0, n) (checked on the device before the traversal;
 //     the CSR itself is not validated).
-//   * The scratch (about 3.7 MB) is part of the library image: every GPU on which the
+//   * The scratch (about 4.2 MB) is part of the library image: every GPU on which the
 //     library is loaded holds it until the process exits.
 //   * All calls of a process share the one array.  The entry point clears what must start
 //     cleared at the beginning of every call and holds a lock until the call's work is
@@ -49,7 +49,7 @@ constexpr size_t o_loff = o_CD + al256(kN2 * 4);
 constexpr size_t o_leoff = o_loff + al256(kN2 * 4);
 constexpr size_t o_sig = o_leoff + al256(kN2 * 4);
 constexpr size_t o_acc = o_sig + al256(kN2 * 8);
-constexpr size_t o_r = o_acc + al256(kN2 * 8);
+constexpr size_t o_r = o_acc + al256(kN2 * 16);
 constexpr size_t o_xm = o_r + al256(kN2 * 8);
 constexpr size_t o_xe = o_xm + al256(kN2 * 8);
 constexpr size_t o_ovf = o_xe + al256(kN2 * 4);
@@ -67,7 +67,7 @@ __global__ void k_noalloc_clear(unsigned char *base, int n) {
   const size_t N = (size_t)n + 2, NW = (size_t)n / 32 + 1;
   int32_t *depth = (int32_t *)(base + o_depth);
   unsigned long long *sig = (unsigned long long *)(base + o_sig);
-  double *acc = (double *)(base + o_acc);
+  unsigned long long *acc = (unsigned long long *)(base + o_acc);
   int32_t *xe = (int32_t *)(base + o_xe);
   uint32_t *ovf = (uint32_t *)(base + o_ovf), *vis = (uint32_t *)(base + o_vis),
            *front = (uint32_t *)(base + o_front);
@@ -75,7 +75,8 @@ __global__ void k_noalloc_clear(unsigned char *base, int n) {
        i += (size_t)gridDim.x * blockDim.x) {
     depth[i] = -1;
     sig[i] = 0ull;
-    acc[i] = 0.0;
+    acc[2 * i] = 0ull;
+    acc[2 * i + 1] = 0ull;
     xe[i] = 0;
     if (i < NW) {
       ovf[i] = 0u;
@@ -149,7 +150,7 @@ extern "C" bc_status bc_sources_noalloc(int32_t n, const int32_t *row_ptr, const
   ws.lvl_off = (int32_t *)(base + o_loff);
   ws.lvl_eoff = (int32_t *)(base + o_leoff);
   ws.sig = (unsigned long long *)(base + o_sig);
-  ws.acc = (double *)(base + o_acc);
+  ws.acc = (unsigned long long *)(base + o_acc);
   ws.r = (double *)(base + o_r);
   ws.xm = (double *)(base + o_xm);
   ws.xe = (int32_t *)(base + o_xe);

@@ -22,9 +22,12 @@
 //     overflows also get an extended-range value (double mantissa, int exponent).
 // Backward (dependency accumulation, Alg. 4 / Alg. 5, successor checking):
 //   for depth = D-1 .. 1, every edge (w, v) of the depth-level vertices w with
-//   d[v] = d[w] + 1 adds r[v] = (1 + delta[v] + omega[v]) / sigma[v] to acc[w]
-//   (warp-segmented sums, one atomic per segment); then delta[w] = sigma[w] * acc[w]
-//   (updateDep), BC[w] += (omega[s] + 1) * delta[w] (Eq. 3 / Eq. 4).
+//   d[v] = d[w] + 1 adds sigma[w] * r[v] = sigma[w] / sigma[v] * (1 + delta[v] + omega[v])
+//   to acc[w]; then delta[w] = acc[w] (updateDep), BC[w] += (omega[s] + 1) * delta[w]
+//   (Eq. 3 / Eq. 4) and r[w] = (1 + delta[w] + omega[w]) / sigma[w].  Each term lies in
+//   [0, n] and is added as a 128-bit fixed-point integer (64 fraction bits; warp-segmented
+//   sums, one pair of 64-bit integer atomics per segment): integer sums do not depend on
+//   the order of the additions, so the result repeats bit for bit from run to run.
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -47,6 +50,7 @@ struct WarpWin {
   int v[WIN];       // vertex of each entry
   int bias[WIN];    // row_ptr[v] - CD: col position of edge e is e + bias
   int ex[WIN];      // extended-range exponent of the owner (backward, EXT only)
+  double sg[WIN];   // sigma of the owner (backward; EXT: its mantissa)
 };
 constexpr size_t kSmemBytes = sizeof(WarpWin) * kWarps;
 
@@ -64,7 +68,8 @@ struct PK {
   int32_t *depth, *Q, *CD, *lvl_off, *lvl_eoff;
   unsigned long long *sig;
   uint32_t *ovf, *vis, *front;
-  double *acc, *r, *xm;
+  unsigned long long *acc;  // [2n]: per vertex the low and high word of a 64.64 fixed-point sum
+  double *r, *xm;
   int32_t *xe;
   PlainCtl *ctl;
   int32_t *out_depth;
@@ -177,7 +182,7 @@ __device__ __forceinline__ void warp_append_u(const PK &p, const int (&w)[U], co
   }
 }
 
-template <bool EXT>
+template <bool EXT, bool BWD>
 __device__ __forceinline__ void fill_window(const PK &p, WarpWin &W, int base, int q1, int E1) {
   const int lane = lane_id();
   int vv[U], cc[U];
@@ -194,7 +199,15 @@ __device__ __forceinline__ void fill_window(const PK &p, WarpWin &W, int base, i
     W.cd[j] = cc[k];
     W.v[j] = vv[k];
     W.bias[j] = vv[k] >= 0 ? p.rp[vv[k]] - cc[k] : 0;
-    if (EXT) W.ex[j] = vv[k] >= 0 ? get_xs(p, vv[k]).e : 0;
+    if (BWD) {
+      if (EXT) {
+        const XS x = vv[k] >= 0 ? get_xs(p, vv[k]) : XS{0.0, 0};
+        W.ex[j] = x.e;
+        W.sg[j] = x.m;
+      } else {
+        W.sg[j] = vv[k] >= 0 ? (double)p.sig[vv[k]] : 0.0;
+      }
+    }
   }
   if (lane == 0) W.cd[WIN] = (base + WIN < q1) ? p.CD[base + WIN] : E1;
   __syncwarp();
@@ -210,7 +223,7 @@ __device__ __forceinline__ int win_owner(const WarpWin &W, int e) {
 
 // Iterate the warp's slice of the edge range [E0, E1) of queue range [q0, q1), U x 32
 // edges at a time.  body(e0, ee) is called once per window with the window filled.
-template <bool EXT, typename F>
+template <bool EXT, bool BWD, typename F>
 __device__ __forceinline__ void edge_windows(const PK &p, WarpWin &W, int q0, int q1, int E0,
                                              int E1, int gwarp, int nwarps, F &&body) {
   long long E = (long long)E1 - E0;
@@ -223,7 +236,7 @@ __device__ __forceinline__ void edge_windows(const PK &p, WarpWin &W, int q0, in
   const int ee = (int)min(ebl + per, (long long)E1);
   int base = warp_find_owner(p.CD, q0, q1, eb);
   for (int e0 = eb; e0 < ee; e0 += WIN) {
-    fill_window<EXT>(p, W, base, q1, E1);
+    fill_window<EXT, BWD>(p, W, base, q1, E1);
     body(e0, ee);
     // next window starts at the owner of edge e0 + WIN
     int jl = win_owner(W, e0 + WIN - 1);
@@ -236,7 +249,7 @@ __device__ __forceinline__ void edge_windows(const PK &p, WarpWin &W, int q0, in
 __device__ void expand_topdown(const PK &p, WarpWin &W, int level, int q0, int q1, int E0,
                                int E1, int gwarp, int nwarps, bool fast) {
   const int lane = lane_id();
-  edge_windows<false>(p, W, q0, q1, E0, E1, gwarp, nwarps, [&](int e0, int ee) {
+  edge_windows<false, false>(p, W, q0, q1, E0, E1, gwarp, nwarps, [&](int e0, int ee) {
     int w[U], v[U];
     bool isnew[U], dag[U];
 #pragma unroll
@@ -351,12 +364,32 @@ __device__ void ext_sigma(const PK &p, int w, int level) {
   p.xe[w] = a.e;
 }
 
+// A term t in [0, 2^63) as a 128-bit fixed-point integer with 64 fraction bits (hi: integer
+// part, lo: fraction), truncated below 2^-64; integer operations on the IEEE-754 fields.
+__device__ __forceinline__ void fx_from(double t, unsigned long long &hi, unsigned long long &lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+  const int ex = (int)((b >> 52) & 0x7ffull);
+  hi = lo = 0ull;
+  if (ex == 0 || (b >> 63)) return;  // zero (or below 2^-1022: far below 2^-64)
+  const unsigned long long m = (b & 0x000fffffffffffffull) | (1ull << 52);  // t = m 2^(ex - 1075)
+  const int sh = ex - 1075 + 64;                                           // fixed = m 2^sh
+  if (sh >= 64) {
+    hi = m << (sh - 64);
+  } else if (sh > 0) {
+    hi = m >> (64 - sh);
+    lo = m << sh;
+  } else if (sh > -64) {
+    lo = m >> (-sh);
+  }
+}
+
 template <bool EXT>
 __device__ void accumulate_level(const PK &p, WarpWin &W, int d, int q0, int q1, int E0, int E1,
                                  int gwarp, int nwarps) {
   const int lane = lane_id();
-  edge_windows<EXT>(p, W, q0, q1, E0, E1, gwarp, nwarps, [&](int e0, int ee) {
+  edge_windows<EXT, true>(p, W, q0, q1, E0, E1, gwarp, nwarps, [&](int e0, int ee) {
     int own[U], nb[U], ew[U];
+    double sw[U];
 #pragma unroll
     for (int k = 0; k < U; k++) {
       int e = e0 + lane + 32 * k;
@@ -364,6 +397,7 @@ __device__ void accumulate_level(const PK &p, WarpWin &W, int d, int q0, int q1,
       bool valid = e < ee;
       own[k] = valid ? W.v[j] : -1;
       ew[k] = EXT ? W.ex[j] : 0;
+      sw[k] = W.sg[j];
       nb[k] = valid ? p.ci[e + W.bias[j]] : -1;
     }
     int dv[U];
@@ -376,21 +410,33 @@ __device__ void accumulate_level(const PK &p, WarpWin &W, int d, int q0, int q1,
       if (dv[k] == d + 1) {
         val[k] = p.r[nb[k]];
         if (EXT) val[k] = ldexp(val[k], ew[k] - p.xe[nb[k]]);
+        val[k] *= sw[k];  // sigma[w] / sigma[v] * (1 + delta[v] + omega[v])
       }
     }
 #pragma unroll
     for (int k = 0; k < U; k++) {
-      double x = val[k];
-      int o = own[k];
+      unsigned long long hi, lo;
+      fx_from(val[k], hi, lo);
+      const int o = own[k];
 #pragma unroll
       for (int s = 1; s < 32; s <<= 1) {
-        double y = __shfl_down_sync(BC_FULL, x, s);
-        int oo = __shfl_down_sync(BC_FULL, o, s);
-        if (lane + s < 32 && oo == o) x += y;
+        const unsigned long long yl = __shfl_down_sync(BC_FULL, lo, s);
+        const unsigned long long yh = __shfl_down_sync(BC_FULL, hi, s);
+        const int oo = __shfl_down_sync(BC_FULL, o, s);
+        if (lane + s < 32 && oo == o) {
+          const unsigned long long l2 = lo + yl;
+          hi += yh + (l2 < lo ? 1ull : 0ull);
+          lo = l2;
+        }
       }
-      int prev = __shfl_up_sync(BC_FULL, o, 1);
-      bool head = (lane == 0) || (prev != o);
-      if (head && o >= 0 && x != 0.0) atomicAdd(p.acc + o, x);
+      const int prev = __shfl_up_sync(BC_FULL, o, 1);
+      const bool head = (lane == 0) || (prev != o);
+      if (head && o >= 0 && (hi | lo)) {
+        unsigned long long *a = p.acc + 2 * (size_t)o;
+        const unsigned long long old = lo ? atomicAdd(a, lo) : 0ull;
+        const unsigned long long c = (lo && old + lo < old) ? 1ull : 0ull;  // the low word wrapped
+        if (hi + c) atomicAdd(a + 1, hi + c);
+      }
     }
   });
 }
@@ -399,8 +445,13 @@ template <bool EXT>
 __device__ void finalize_level(const PK &p, int q0, int q1, double ws, int gtid, int nthr) {
   for (int i = q0 + gtid; i < q1; i += nthr) {
     int w = p.Q[i];
-    double a = p.acc[w];
-    if (a != 0.0) p.acc[w] = 0.0;
+    unsigned long long *a = p.acc + 2 * (size_t)w;
+    const unsigned long long lo = a[0], hi = a[1];
+    if (lo | hi) {
+      a[0] = 0ull;
+      a[1] = 0ull;
+    }
+    const double delta = (double)hi + (double)lo * 0x1p-64;
     double om = p.omega ? (double)p.omega[w] : 0.0;
     double sg;
     if (EXT) {
@@ -410,8 +461,7 @@ __device__ void finalize_level(const PK &p, int q0, int q1, double ws, int gtid,
     } else {
       sg = (double)p.sig[w];
     }
-    double delta = sg * a;
-    if (a != 0.0) p.bc[w] += ws * delta;
+    if (lo | hi) p.bc[w] += ws * delta;
     p.r[w] = (1.0 + delta + om) / sg;
   }
 }
@@ -673,7 +723,7 @@ bc_status plain_setup(int *blocks_per_sm) {
 
 int64_t plain_bytes(int32_t n) {
   int64_t N = n + 2, nw = (n + 31) / 32 + 1;
-  return N * (4 * 5 + 8 * 5) + nw * 4 * 3 + (int64_t)sizeof(PlainCtl) + 4096;
+  return N * (4 * 5 + 8 * 6) + nw * 4 * 3 + (int64_t)sizeof(PlainCtl) + 4096;
 }
 
 void plain_free(Ctx *ctx, PlainWS *ws) {
@@ -692,7 +742,7 @@ static bc_status plain_reset(PlainWS *ws, cudaStream_t st) {
   BC_CUDA_TRY(cudaMemsetAsync(ws->ovf, 0, nw * 4, st));
   BC_CUDA_TRY(cudaMemsetAsync(ws->vis, 0, nw * 4, st));
   BC_CUDA_TRY(cudaMemsetAsync(ws->front, 0, nw * 4, st));
-  BC_CUDA_TRY(cudaMemsetAsync(ws->acc, 0, N * 8, st));
+  BC_CUDA_TRY(cudaMemsetAsync(ws->acc, 0, N * 16, st));
   BC_CUDA_TRY(cudaMemsetAsync(ws->xe, 0, N * 4, st));
   BC_CUDA_TRY(cudaMemsetAsync(ws->ctl, 0, sizeof(PlainCtl), st));
   return BC_OK;
@@ -709,7 +759,7 @@ bc_status plain_ensure(Ctx *ctx, PlainWS *ws, int32_t n) {
 #define PA(ptr, bytes) \
   if (e == cudaSuccess) e = cudaMalloc((void **)&ws->ptr, (bytes));
   PA(depth, N * 4) PA(Q, N * 4) PA(CD, N * 4) PA(lvl_off, N * 4) PA(lvl_eoff, N * 4)
-  PA(sig, N * 8) PA(ovf, nw * 4) PA(vis, nw * 4) PA(front, nw * 4) PA(acc, N * 8)
+  PA(sig, N * 8) PA(ovf, nw * 4) PA(vis, nw * 4) PA(front, nw * 4) PA(acc, N * 16)
   PA(r, N * 8) PA(xm, N * 8) PA(xe, N * 4) PA(ctl, sizeof(PlainCtl))
 #undef PA
   ws->n = n;

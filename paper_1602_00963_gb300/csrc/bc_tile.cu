@@ -32,11 +32,12 @@
 // source lanes.  Levels whose entries average at most two sources and 16 edges (high-
 // diameter graphs) run one entry per lane instead.  Vertices of degree >= kHub are
 // processed by whole CTAs (forward) or as 4096-edge items spread over CTAs (backward).
-// Warp-level work is numbered across CTAs first.  σ, depth and the masks are exact.  The
-// float-float r sums of an entry walked warp-wide take each 32-edge step's two-source hits
-// before its row gathers, and where the steps fall depends on the ranges the warps claim
-// at run time, so r and BC can differ in the last bits from one run to the next; the
-// lane-per-entry mode and the hub items sum in a fixed order.
+// Warp-level work is numbered across CTAs first.  σ, depth and the masks are exact.  Every
+// floating-point sum has a fixed order: an entry walked warp-wide adds its hits in edge
+// order (wherever the warps' run-time range claims put the 32-edge steps), the lane-per-
+// entry mode walks an entry's edges in order, hub items split an adjacency at fixed
+// offsets and their partials are summed in chunk order, and BC takes one update per
+// (vertex, level) in level order.  So r and BC repeat bit for bit from run to run.
 //
 // sigma beyond 2^64: a tile first runs with r computed from sigma mod 2^64; if any count
 // overflowed, the tile is rerun (before any BC update) in extended mode, where each
@@ -114,7 +115,7 @@ struct TileWS {
   float2 *r = nullptr;  // float-float r values
   double *xm = nullptr;
   int32_t *xe = nullptr;
-  int32_t *A = nullptr, *ACD = nullptr;
+  int32_t *A = nullptr, *ACD = nullptr, *ARP = nullptr;
   uint32_t *AM = nullptr;
   int32_t *Aoff = nullptr;
   unsigned long long *Lbits = nullptr;
@@ -123,13 +124,13 @@ struct TileWS {
   float2 *Hpart = nullptr;                   // per-item partial sums (one level's items)
   int64_t hpart_items = 0;
   size_t bytes_hpart = 0;
-  int32_t *C = nullptr, *CPD = nullptr, *Ch = nullptr;
+  int32_t *C = nullptr, *CPD = nullptr, *CRP = nullptr, *Ch = nullptr;
   float2 *wsrc = nullptr;
   TileCtl *ctl = nullptr;
   size_t bytes_main = 0, bytes_ext = 0, bytes_A = 0;
   // per-graph lists: hubs (degree >= kHub) and the bottom-up walk list (others, deg > 0)
   const int32_t *lists_for = nullptr;
-  int32_t *hubs = nullptr, *Lbu = nullptr, *PDbu = nullptr;
+  int32_t *hubs = nullptr, *Lbu = nullptr, *PDbu = nullptr, *RPbu = nullptr;
   int nhubs = 0, nbu = 0, Ebu = 0;
   size_t bytes_lists = 0;
 };
@@ -151,7 +152,7 @@ struct TK {
   float2 *r;  // r = (1 + delta + omega) / sigma per (vertex, source), float-float
   double *xm;
   int32_t *xe;
-  int32_t *A, *ACD;
+  int32_t *A, *ACD, *ARP;  // active list: vertex, level-relative edge prefix, row_ptr of the vertex
   uint32_t *AM;
   long long capA;
   int32_t *Aoff;
@@ -159,8 +160,8 @@ struct TK {
   int32_t *HE, *HEoff;
   int32_t *HEk, *Hdone;  // backward hub items: chunk number; finished chunks of the entry
   float2 *Hpart;         // [items of a level][T] partial r sums of hub chunks
-  int32_t *C, *CPD, *Ch;
-  const int32_t *hubs, *Lbu, *PDbu;
+  int32_t *C, *CPD, *CRP, *Ch;
+  const int32_t *hubs, *Lbu, *PDbu, *RPbu;
   int nhubs, nbu, Ebu;
   float2 *wsrc;  // per source: omega(s) + 1, float-float
   TileCtl *ctl;
@@ -226,7 +227,8 @@ __device__ __forceinline__ void append_A(const TK &p, unsigned long long *ctr, i
                                          bool flag, int v) {
   unsigned m = __ballot_sync(BC_FULL, flag);
   if (!m) return;
-  int deg = flag ? vdeg(p, v) : 0;
+  const int r0 = flag ? p.rp[v] : 0;
+  int deg = flag ? p.rp[v + 1] - r0 : 0;
   int tot;
   int pre = warp_excl_scan(deg, &tot);
   unsigned long long b = 0;
@@ -238,6 +240,7 @@ __device__ __forceinline__ void append_A(const TK &p, unsigned long long *ctr, i
     if (pos < p.capA) {
       p.A[pos] = v;
       p.ACD[pos] = (int)(b & 0xffffffffull) + pre;
+      p.ARP[pos] = r0;
       if (deg >= kHub) {  // hubs are also listed for the backward sweep, one item per chunk
         const int nch = (deg + kHubChunk - 1) / kHubChunk;
         const int hp = atomicAdd(&p.ctl->hecnt, nch);
@@ -303,15 +306,19 @@ __device__ __forceinline__ int find_owner(const int32_t *PD, int lo, int hi, int
   return lo + (31 - __clz(b));
 }
 
-// Walk the adjacency of list entries [i_lo, i_hi) (entry i: vertex L[i] whose edges
-// start at the level-relative prefix PD[i]; E edges in all), restricted to the entries
-// that start inside the edge range [eb, ee): ranges are snapped to entry starts, so each
-// entry is walked by exactly one warp.  With SKIP_HUBS, entries of degree >= kHub are
-// jumped over.  f(valid, k, w, col) is called once per 32-edge step (lane = edge) with the
-// warp converged: k = entry, w = its vertex, col = position of the edge in col_idx.
+// Walk the adjacency of list entries [i_lo, i_hi) (entry i: vertex L[i], whose row starts
+// at RP[i] = row_ptr[L[i]] and whose edges start at the level-relative prefix PD[i]; E edges
+// in all), restricted to the entries that start inside the edge range [eb, ee): ranges are
+// snapped to entry starts, so each entry is walked by exactly one warp.  With SKIP_HUBS,
+// entries of degree >= kHub are jumped over (an entry's degree is the difference of
+// consecutive prefixes, already in registers).  f(valid, k, w, col) is called once per
+// 32-edge step (lane = edge) with the warp converged: k = entry, w = its vertex, col =
+// position of the edge in col_idx.  A step's window of 32 entries is one round of
+// independent loads (PD, L, RP).
 template <bool SKIP_HUBS, typename F>
-__device__ __forceinline__ void walk_range(const TK &p, const int32_t *L, const int32_t *PD, int i_lo,
-                                           int i_hi, int E, int eb, int ee, F &&f) {
+__device__ __forceinline__ void walk_range(const TK &p, const int32_t *L, const int32_t *PD,
+                                           const int32_t *RP, int i_lo, int i_hi, int E, int eb, int ee,
+                                           F &&f) {
   const int lane = lane_id();
   int i0 = find_owner(PD, i_lo, i_hi, eb);
   if (PD[i0] < eb) i0++;
@@ -320,23 +327,28 @@ __device__ __forceinline__ void walk_range(const TK &p, const int32_t *L, const 
   const int e_end = (i1 < i_hi) ? PD[i1] : E;
   int base = i0, e = PD[i0];
   while (e < e_end) {
-    if (SKIP_HUBS && PD[base] == e && vdeg(p, L[base]) >= kHub) {
-      base++;
-      e = (base < i1) ? PD[base] : e_end;
-      continue;
-    }
     const int idx = base + lane;
     const bool in = idx < i1;
     const int cd = in ? PD[idx] : INT_MAX;
     const int vv = in ? L[idx] : 0;
-    const int bias = in ? p.rp[vv] - cd : 0;
+    const int bias = in ? RP[idx] - cd : 0;
     const int cd_after = (base + 32 < i1) ? PD[base + 32] : e_end;
+    // prefix of the next entry (its edges' start), so degree = nx - cd
+    int nx = __shfl_down_sync(BC_FULL, cd, 1);
+    if (lane == 31) nx = cd_after;
+    if (idx + 1 >= i1) nx = e_end;
+    const unsigned hubm = SKIP_HUBS ? __ballot_sync(BC_FULL, in && nx - cd >= kHub) : 0u;
+    if (SKIP_HUBS && (hubm & 1u)) {  // the step would start inside a hub: jump over it
+      e = __shfl_sync(BC_FULL, nx, 0);
+      base++;
+      continue;
+    }
     const int my = e + lane;
     const int j = warp_owner(cd, my);
     const int w = __shfl_sync(BC_FULL, vv, j);
     const int col = my + __shfl_sync(BC_FULL, bias, j);
     bool valid = my < e_end;
-    if (SKIP_HUBS && valid) valid = vdeg(p, w) < kHub;
+    if (SKIP_HUBS) valid = valid && !((hubm >> j) & 1u);
     f(valid, base + j, w, col);
     const int j31 = __shfl_sync(BC_FULL, j, 31);
     int nxt = __shfl_sync(BC_FULL, cd, min(j31 + 1, 31));
@@ -344,10 +356,6 @@ __device__ __forceinline__ void walk_range(const TK &p, const int32_t *L, const 
     const int nb = base + j31 + ((e + 32 >= nxt) ? 1 : 0);
     e += 32;
     base = nb;
-    if (SKIP_HUBS && e < e_end && base < i1 && vdeg(p, L[base]) >= kHub) {
-      base++;
-      e = (base < i1) ? PD[base] : e_end;
-    }
   }
 }
 
@@ -359,8 +367,9 @@ __device__ __forceinline__ void walk_range(const TK &p, const int32_t *L, const 
 constexpr int kChunk = 1024;
 
 template <bool SKIP_HUBS, typename F>
-__device__ __forceinline__ void walk(const TK &p, const int32_t *L, const int32_t *PD, int i_lo,
-                                     int i_hi, int E, int gwarp, int nwarps, unsigned long long *ctr, F &&f) {
+__device__ __forceinline__ void walk(const TK &p, const int32_t *L, const int32_t *PD, const int32_t *RP,
+                                     int i_lo, int i_hi, int E, int gwarp, int nwarps, unsigned long long *ctr,
+                                     F &&f) {
   if (E <= 0 || i_hi <= i_lo) return;
   long long ch = ((long long)E / (4ll * nwarps) + 31) & ~31ll;
   ch = ch < 32 ? 32 : (ch > kChunk ? kChunk : ch);
@@ -386,7 +395,7 @@ __device__ __forceinline__ void walk(const TK &p, const int32_t *L, const int32_
       nb = min(base0 + off, (long long)E);
       ne = min(nb + sz, (long long)E);
     }
-    walk_range<SKIP_HUBS>(p, L, PD, i_lo, i_hi, E, (int)eb, (int)ee, f);
+    walk_range<SKIP_HUBS>(p, L, PD, RP, i_lo, i_hi, E, (int)eb, (int)ee, f);
     eb = nb;
     ee = ne;
   }
@@ -428,7 +437,9 @@ __device__ __forceinline__ void pull_hit(const TK &p, int pn, const uint32_t (&m
       const unsigned long long sv = p.sig[idx];
       const unsigned long long old = a.s[g];
       a.s[g] = old + sv;
-      const bool po = (p.ovf[(size_t)pn * G + g] >> lane) & 1u;
+      // 64-bit mode: an overflowed parent has already flagged the tile for the extended
+      // rerun, so only this addition's carry is checked
+      const bool po = EXT && ((p.ovf[(size_t)pn * G + g] >> lane) & 1u);
       if (a.s[g] < old || po) a.o |= 1u << g;
       if (EXT) {
         XS y;
@@ -559,11 +570,11 @@ __device__ __forceinline__ void fwd_hit_load(const TK &p, FwdHit<G, EXT> &h) {
   if (!h.sp) return;
   const size_t i0 = (size_t)h.pj * (32 * G) + h.t0;
   h.s0 = p.sig[i0];
-  h.o0 = (p.ovf[(size_t)h.pj * G + (h.t0 >> 5)] >> (h.t0 & 31)) & 1u;
+  h.o0 = EXT && ((p.ovf[(size_t)h.pj * G + (h.t0 >> 5)] >> (h.t0 & 31)) & 1u);
   const size_t i1 = (size_t)h.pj * (32 * G) + (h.t1 >= 0 ? h.t1 : h.t0);
   if (h.t1 >= 0) {
     h.s1 = p.sig[i1];
-    h.o1 = (p.ovf[(size_t)h.pj * G + (h.t1 >> 5)] >> (h.t1 & 31)) & 1u;
+    h.o1 = EXT && ((p.ovf[(size_t)h.pj * G + (h.t1 >> 5)] >> (h.t1 & 31)) & 1u);
   }
   if (EXT) {
     if (h.o0) {
@@ -585,60 +596,68 @@ __device__ __forceinline__ void fwd_hit_load(const TK &p, FwdHit<G, EXT> &h) {
 
 // Add the hits of lanes hs (sparse) and hd (the others), all of one owner, to a: sparse
 // terms by shuffles, the others by sigma-row gathers (HB<G> rows in flight together).
+// Integer sums do not depend on their order; the extended-range sums (EXT) are floating
+// point, so there every hit is taken in lane (edge) order, sparse or not.
+template <int G, bool EXT>
+__device__ __forceinline__ void fwd_sparse_take(const FwdHit<G, EXT> &h, int jj, PullAcc<G, EXT> &a) {
+  const int u0 = __shfl_sync(BC_FULL, h.t0, jj), u1 = __shfl_sync(BC_FULL, h.t1, jj);
+  XS y0, y1;
+  y0.m = y1.m = 0.0;
+  y0.e = y1.e = 0;
+  if (EXT) {
+    y0.m = __shfl_sync(BC_FULL, h.x0.m, jj);
+    y0.e = __shfl_sync(BC_FULL, h.x0.e, jj);
+  }
+  pull_sparse_add<G, EXT>(a, u0, __shfl_sync(BC_FULL, h.s0, jj), __shfl_sync(BC_FULL, h.o0, jj), y0);
+  if (u1 >= 0) {
+    if (EXT) {
+      y1.m = __shfl_sync(BC_FULL, h.x1.m, jj);
+      y1.e = __shfl_sync(BC_FULL, h.x1.e, jj);
+    }
+    pull_sparse_add<G, EXT>(a, u1, __shfl_sync(BC_FULL, h.s1, jj), __shfl_sync(BC_FULL, h.o1, jj), y1);
+  }
+}
+
 template <int G, bool EXT>
 __device__ __forceinline__ void fwd_hits_add(const TK &p, const FwdHit<G, EXT> &h, unsigned hs, unsigned hd,
                                              PullAcc<G, EXT> &a) {
   const int lane = lane_id();
-  while (hs) {
-    const int jj = __ffs(hs) - 1;
-    hs &= hs - 1;
-    const int u0 = __shfl_sync(BC_FULL, h.t0, jj), u1 = __shfl_sync(BC_FULL, h.t1, jj);
-    XS y0, y1;
-    y0.m = y1.m = 0.0;
-    y0.e = y1.e = 0;
-    if (EXT) {
-      y0.m = __shfl_sync(BC_FULL, h.x0.m, jj);
-      y0.e = __shfl_sync(BC_FULL, h.x0.e, jj);
-    }
-    pull_sparse_add<G, EXT>(a, u0, __shfl_sync(BC_FULL, h.s0, jj), __shfl_sync(BC_FULL, h.o0, jj), y0);
-    if (u1 >= 0) {
-      if (EXT) {
-        y1.m = __shfl_sync(BC_FULL, h.x1.m, jj);
-        y1.e = __shfl_sync(BC_FULL, h.x1.e, jj);
-      }
-      pull_sparse_add<G, EXT>(a, u1, __shfl_sync(BC_FULL, h.s1, jj), __shfl_sync(BC_FULL, h.o1, jj), y1);
-    }
-  }
   if (EXT) {
-    while (hd) {
-      const int jj = __ffs(hd) - 1;
-      hd &= hd - 1;
-      uint32_t m[G];
+    unsigned hm = hs | hd;
+    while (hm) {
+      const int jj = __ffs(hm) - 1;
+      hm &= hm - 1;
+      if ((hs >> jj) & 1u) {
+        fwd_sparse_take<G, EXT>(h, jj, a);
+      } else {
+        uint32_t m[G];
 #pragma unroll
-      for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, h.bm[g], jj);
-      pull_hit<G, EXT>(p, __shfl_sync(BC_FULL, h.pj, jj), m, a);
+        for (int g = 0; g < G; g++) m[g] = __shfl_sync(BC_FULL, h.bm[g], jj);
+        pull_hit<G, EXT>(p, __shfl_sync(BC_FULL, h.pj, jj), m, a);
+      }
     }
     return;
   }
+  while (hs) {
+    const int jj = __ffs(hs) - 1;
+    hs &= hs - 1;
+    fwd_sparse_take<G, EXT>(h, jj, a);
+  }
+  // 64-bit mode (EXT is handled above): an overflowed parent has already flagged the tile
+  // for the extended rerun, so only the additions' carries are checked
   while (hd) {
     unsigned long long sv[HB<G>::value][G];
     uint32_t mq[HB<G>::value][G];
-    uint32_t povf[HB<G>::value];
 #pragma unroll
     for (int q = 0; q < HB<G>::value; q++) {
       const int jq = hd ? __ffs(hd) - 1 : -1;
       if (hd) hd &= hd - 1;
       const int pn = __shfl_sync(BC_FULL, h.pj, jq < 0 ? 0 : jq);
-      povf[q] = 0u;
 #pragma unroll
       for (int g = 0; g < G; g++) {
         const uint32_t m = __shfl_sync(BC_FULL, h.bm[g], jq < 0 ? 0 : jq);
         mq[q][g] = jq < 0 ? 0u : m;
-        sv[q][g] = 0ull;
-        if ((mq[q][g] >> lane) & 1u) {
-          sv[q][g] = p.sig[(size_t)pn * (32 * G) + 32 * g + lane];
-          if ((p.ovf[(size_t)pn * G + g] >> lane) & 1u) povf[q] |= 1u << g;
-        }
+        sv[q][g] = ((mq[q][g] >> lane) & 1u) ? p.sig[(size_t)pn * (32 * G) + 32 * g + lane] : 0ull;
       }
     }
 #pragma unroll
@@ -648,7 +667,7 @@ __device__ __forceinline__ void fwd_hits_add(const TK &p, const FwdHit<G, EXT> &
         a.newm[g] |= mq[q][g];
         const unsigned long long old = a.s[g];
         a.s[g] = old + sv[q][g];
-        if (a.s[g] < old || ((povf[q] >> g) & 1u)) a.o |= 1u << g;
+        if (a.s[g] < old) a.o |= 1u << g;
       }
     }
   }
@@ -659,7 +678,7 @@ __device__ __forceinline__ void fwd_hits_add(const TK &p, const FwdHit<G, EXT> &
 // and the other hits (sigma rows gathered by the source lanes) are summed, each set in
 // edge order.
 template <int G, bool EXT>
-__device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_t *PD, int n_list,
+__device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_t *PD, const int32_t *RP, int n_list,
                           int E, int gwarp, int nwarps, AppendBuf &ab, unsigned long long *ap,
                           int a_base, bool leaf, unsigned long long (&nsacc)[G]) {
   const uint32_t *Fp = Fbuf<G>(p, level - 1);
@@ -669,7 +688,7 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
   pull_init(a);
 #pragma unroll
   for (int g = 0; g < G; g++) visc[g] = 0u;
-  walk<false>(p, L, PD, 0, n_list, E, gwarp, nwarps, &p.ctl->wq[level % 3],
+  walk<false>(p, L, PD, RP, 0, n_list, E, gwarp, nwarps, &p.ctl->wq[level % 3],
               [&](bool valid, int k, int w, int col) {
     uint32_t vw[G];
     FwdHit<G, EXT> h;
@@ -679,11 +698,13 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
       h.bm[g] = 0u;
     }
     bool full = true;
+    // the owner's visited row and the edge's neighbour are independent loads
+    const int pj = valid ? p.ci[col] : -1;
     if (valid) full = load_vis<G>(p, w, vw);
     h.pj = -1;
     h.hit = false;
     if (valid && !full) {
-      h.pj = p.ci[col];
+      h.pj = pj;
       load_row<G>(Fp, h.pj, h.bm);
 #pragma unroll
       for (int g = 0; g < G; g++) {
@@ -875,7 +896,7 @@ __device__ __forceinline__ void lane_pull(const TK &p, const uint32_t *Fp, int w
           const int t = 32 * g + bit;
           const size_t idx = (size_t)pj[u] * (32 * G) + t;
           const unsigned long long v = p.sig[idx];
-          const bool po = (p.ovf[(size_t)pj[u] * G + g] >> bit) & 1u;
+          const bool po = EXT && ((p.ovf[(size_t)pj[u] * G + g] >> bit) & 1u);
           XS x;
           x.m = 0.0;
           x.e = 0;
@@ -925,7 +946,7 @@ __device__ __forceinline__ void lane_pull_pair(const TK &p, const uint32_t *Fp, 
         if (sl.t < 0 || !((f >> (sl.t & 31)) & 1u)) continue;
         const size_t idx = (size_t)pj[u] * (32 * G) + sl.t;
         const unsigned long long v = p.sig[idx];
-        const bool po = (p.ovf[(size_t)pj[u] * G + (sl.t >> 5)] >> (sl.t & 31)) & 1u;
+        const bool po = EXT && ((p.ovf[(size_t)pj[u] * G + (sl.t >> 5)] >> (sl.t & 31)) & 1u);
         XS x;
         x.m = 0.0;
         x.e = 0;
@@ -1112,6 +1133,7 @@ __device__ void init_sources(const TK &p) {
       if (first) {
         p.A[cnt] = s;
         p.ACD[cnt] = (int)edges;
+        p.ARP[cnt] = p.rp[s];
         cnt++;
         edges += (unsigned)ds;
       }
@@ -1178,7 +1200,7 @@ __device__ void phase_mark(const TK &p, int level, int a0, int a1, int E1, int g
     const bool in = idx < a1;
     const int cdj = in ? p.ACD[idx] : INT_MAX;
     const int vj = in ? p.A[idx] : 0;
-    const int bias = in ? p.rp[vj] - cdj : 0;
+    const int bias = in ? p.ARP[idx] - cdj : 0;
     const int cd_after = (base + 32 < a1) ? p.ACD[base + 32] : E1;
     const int my = e + lane;
     const int j = warp_owner(cdj, my);
@@ -1199,7 +1221,8 @@ __device__ void phase_mark(const TK &p, int level, int a0, int a1, int E1, int g
         isc = !(atomicOr(p.cand + (w >> 5), bit) & bit);
       }
     }
-    const int dw = isc ? vdeg(p, w) : 0;
+    const int rw = isc ? p.rp[w] : 0;
+    const int dw = isc ? p.rp[w + 1] - rw : 0;
     const bool hub = isc && dw >= kHub;
     const bool nrm = isc && !hub;
     const unsigned mn = __ballot_sync(BC_FULL, nrm), mh = __ballot_sync(BC_FULL, hub);
@@ -1213,6 +1236,7 @@ __device__ void phase_mark(const TK &p, int level, int a0, int a1, int E1, int g
         const int pos = (int)(b >> 32) + __popc(mn & lanemask_lt());
         p.C[pos] = w;
         p.CPD[pos] = (int)(b & 0xffffffffull) + pre;
+        p.CRP[pos] = rw;
       }
     }
     if (mh) {
@@ -1245,7 +1269,7 @@ __device__ void phase_pull(const TK &p, int level, bool bu, int a_lo, int a_base
   ab.v = 0;
   ab.n = 0;
   if (bu) {
-    pull_walk<G, EXT>(p, level, p.Lbu, p.PDbu, p.nbu, p.Ebu, gwarp, nwarps, ab, ap, a_base, leaf, nsacc);
+    pull_walk<G, EXT>(p, level, p.Lbu, p.PDbu, p.RPbu, p.nbu, p.Ebu, gwarp, nwarps, ab, ap, a_base, leaf, nsacc);
   } else {
     const unsigned long long cpk = vload64(&p.ctl->cpack[level % 3]);
     const int nc = (int)(cpk >> 32);
@@ -1255,7 +1279,7 @@ __device__ void phase_pull(const TK &p, int level, bool bu, int a_lo, int a_base
     if (lane_level(vload64(&p.Lbits[level - 1]), a_base - a_lo, (long long)ec) && ec <= 16ll * nc)
       pull_lanes<G, EXT>(p, level, nc, gwarp, nwarps, ap, a_base, leaf, nsacc);
     else
-      pull_walk<G, EXT>(p, level, p.C, p.CPD, nc, ec, gwarp, nwarps, ab, ap, a_base, leaf, nsacc);
+      pull_walk<G, EXT>(p, level, p.C, p.CPD, p.CRP, nc, ec, gwarp, nwarps, ab, ap, a_base, leaf, nsacc);
     // clear the candidate bits of this level (C and Ch)
     for (int i = gwarp * 32 + lane; i < nc; i += nwarps * 32) {
       const int w = p.C[i];
@@ -1316,18 +1340,31 @@ struct BwdOwner {
   uint32_t mw[G];
   float2 sg[G];  // sigma (extended: its mantissa), float-float
   int ew[EXT ? G : 1];
-  float2 acc[G];  // sum of the successors' r
+  float2 acc[G];   // sum of the successors' r: hits gathered as rows
+  float2 accs[G];  // the same for sparse hits (at most two sources), folded in by bwd_fold
 };
 
+// acc = accs + acc (a fixed order), accs = 0: the owner's full sum of the successors' r
 template <int G, bool EXT>
-__device__ __forceinline__ void bwd_start(const TK &p, int k, BwdOwner<G, EXT> &o) {
-  const int lane = lane_id();
-  const int w = p.A[k];
-  load_row<G>(p.AM, k, o.mw);
+__device__ __forceinline__ void bwd_fold(BwdOwner<G, EXT> &o) {
 #pragma unroll
   for (int g = 0; g < G; g++) {
+    float2 t = o.accs[g];
+    ff_add(t, o.acc[g]);
+    o.acc[g] = t;
+    o.accs[g] = make_float2(0.0f, 0.0f);
+  }
+}
+
+template <int G, bool EXT>
+__device__ __forceinline__ void bwd_start(const TK &p, int w, const uint32_t (&mw)[G], BwdOwner<G, EXT> &o) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    o.mw[g] = mw[g];
     o.sg[g] = make_float2(1.0f, 0.0f);
     o.acc[g] = make_float2(0.0f, 0.0f);
+    o.accs[g] = make_float2(0.0f, 0.0f);
     if (EXT) o.ew[g] = 0;
     if ((o.mw[g] >> lane) & 1u) {
       const size_t idx = (size_t)w * (32 * G) + 32 * g + lane;
@@ -1341,6 +1378,14 @@ __device__ __forceinline__ void bwd_start(const TK &p, int k, BwdOwner<G, EXT> &
       }
     }
   }
+}
+
+// The same for entry k of the active list (vertex and masks loaded here).
+template <int G, bool EXT>
+__device__ __forceinline__ void bwd_start_k(const TK &p, int k, BwdOwner<G, EXT> &o) {
+  uint32_t mw[G];
+  load_row<G>(p.AM, k, mw);
+  bwd_start<G, EXT>(p, p.A[k], mw, o);
 }
 
 template <int G, bool EXT>
@@ -1358,8 +1403,9 @@ __device__ __forceinline__ void bwd_hit(const TK &p, int v, const uint32_t (&m)[
 }
 
 template <int G, bool EXT>
-__device__ __forceinline__ void bwd_commit(const TK &p, int w, const BwdOwner<G, EXT> &o) {
+__device__ __forceinline__ void bwd_commit(const TK &p, int w, BwdOwner<G, EXT> &o) {
   const int lane = lane_id();
+  bwd_fold<G, EXT>(o);
   const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
   float2 contrib = make_float2(0.0f, 0.0f);
   float2 dl[G];
@@ -1431,7 +1477,11 @@ __device__ __forceinline__ void bwd_hit_load(const TK &p, BwdHit<G, EXT> &h) {
   }
 }
 
-// Add the hits of lanes hs (sparse) and hd (the others), all of one owner, to o.acc.
+// Add the hits of lanes hs (sparse) and hd (the others), all of one owner: sparse terms by
+// shuffles into o.accs, the others by r-row gathers into o.acc (HB<G> rows in flight
+// together).  Whether a hit is sparse depends on its mask alone, and each of the two sums
+// takes its terms in lane (edge) order, step after step, so both are the same fold of the
+// owner's edges wherever the walk's 32-edge steps fall: the sums repeat bit for bit.
 template <int G, bool EXT>
 __device__ __forceinline__ void bwd_hits_add(const TK &p, const BwdHit<G, EXT> &h, unsigned hs, unsigned hd,
                                              BwdOwner<G, EXT> &o) {
@@ -1446,7 +1496,7 @@ __device__ __forceinline__ void bwd_hits_add(const TK &p, const BwdHit<G, EXT> &
       const int xe = EXT ? __shfl_sync(BC_FULL, z ? h.e1 : h.e0, jj) : 0;
 #pragma unroll
       for (int g = 0; g < G; g++)
-        if (t >= 0 && (t >> 5) == g && lane == (t & 31)) ff_add(o.acc[g], EXT ? ff_scale(x, o.ew[g] - xe) : x);
+        if (t >= 0 && (t >> 5) == g && lane == (t & 31)) ff_add(o.accs[g], EXT ? ff_scale(x, o.ew[g] - xe) : x);
     }
   }
   if (EXT) {
@@ -1490,17 +1540,20 @@ __device__ __forceinline__ void bwd_hits_add(const TK &p, const BwdHit<G, EXT> &
 template <int G, bool EXT>
 __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn, int gwarp,
                          int nwarps, unsigned long long *ctr) {
-  int cur = -1;
+  int cur = -1, cur_w = -1;
   BwdOwner<G, EXT> o;
-  walk<true>(p, p.A, p.ACD, a0, a1, E, gwarp, nwarps, ctr, [&](bool valid, int k, int, int col) {
+  walk<true>(p, p.A, p.ACD, p.ARP, a0, a1, E, gwarp, nwarps, ctr, [&](bool valid, int k, int w, int col) {
     BwdHit<G, EXT> h;
     h.hit = false;
     h.v = -1;
+    uint32_t am[G];  // the owner's level-d mask (each edge lane loads its owner's)
 #pragma unroll
-    for (int g = 0; g < G; g++) h.bm[g] = 0u;
+    for (int g = 0; g < G; g++) {
+      h.bm[g] = 0u;
+      am[g] = 0u;
+    }
     if (valid) {
       h.v = p.ci[col];
-      uint32_t am[G];
       load_row<G>(Dn, h.v, h.bm);
       load_row<G>(p.AM, k, am);
 #pragma unroll
@@ -1520,14 +1573,19 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
       const unsigned lanes_k = __ballot_sync(BC_FULL, valid && k == kk);
       if (!lanes_k) continue;  // a hub entry inside the step
       if (kk != cur) {
-        if (cur >= 0) bwd_commit<G, EXT>(p, p.A[cur], o);
+        if (cur >= 0) bwd_commit<G, EXT>(p, cur_w, o);
+        const int jl = __ffs(lanes_k) - 1;  // a lane of this owner: its vertex and masks
+        uint32_t mw[G];
+#pragma unroll
+        for (int g = 0; g < G; g++) mw[g] = __shfl_sync(BC_FULL, am[g], jl);
         cur = kk;
-        bwd_start<G, EXT>(p, kk, o);
+        cur_w = __shfl_sync(BC_FULL, w, jl);
+        bwd_start<G, EXT>(p, cur_w, mw, o);
       }
       bwd_hits_add<G, EXT>(p, h, sps & lanes_k, dns & lanes_k, o);
     }
   });
-  if (cur >= 0) bwd_commit<G, EXT>(p, p.A[cur], o);
+  if (cur >= 0) bwd_commit<G, EXT>(p, cur_w, o);
 }
 
 template <int G, bool EXT>
@@ -1537,7 +1595,7 @@ __device__ void bwd_hub_item(const TK &p, int i, int h0, const uint32_t *Dn, uns
   const int w = p.A[k];
   const int nch = (vdeg(p, w) + kHubChunk - 1) / kHubChunk;
   BwdOwner<G, EXT> o;
-  bwd_start<G, EXT>(p, k, o);
+  bwd_start_k<G, EXT>(p, k, o);
   const int e0 = p.rp[w] + c * kHubChunk, e1 = min(p.rp[w + 1], e0 + kHubChunk);
   const int per = ((e1 - e0 + nw - 1) / nw + 31) & ~31;
   const int lo = min(e1, e0 + wid * per), hi = min(e1, lo + per);
@@ -1560,6 +1618,7 @@ __device__ void bwd_hub_item(const TK &p, int i, int h0, const uint32_t *Dn, uns
     bwd_hit_load<G, EXT>(p, h);
     bwd_hits_add<G, EXT>(p, h, __ballot_sync(BC_FULL, h.sp), __ballot_sync(BC_FULL, h.hit && !h.sp), o);
   }
+  bwd_fold<G, EXT>(o);
   float2 *sa = (float2 *)smem;
 #pragma unroll 1
   for (int g = 0; g < G; g++) {
@@ -1725,7 +1784,7 @@ __device__ void bwd_lanes(const TK &p, int a0, int a1, const uint32_t *Dn, int g
       fbm &= fbm - 1;
       const int kf = __shfl_sync(BC_FULL, k, j), wf = __shfl_sync(BC_FULL, w, j);
       BwdOwner<G, EXT> o;
-      bwd_start<G, EXT>(p, kf, o);
+      bwd_start_k<G, EXT>(p, kf, o);
       const int e1 = p.rp[wf + 1];
       for (int eb = p.rp[wf]; eb < e1; eb += 32) {
         const int e = eb + lane;
@@ -1855,11 +1914,13 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
     p.ctl->lmax = lmax;
     p.ctl->levels += level - 1;
   }
-  if (fwd_only) return;
+  // 64-bit mode checks only carries, so the overflow flags are exact only in extended
+  // mode: a tile that overflowed reruns there, also when only sigma is exported
   if (!EXT && *(volatile int *)&p.ctl->ovf_any) {
     if (gtid == 0) atomicCAS(&p.ctl->bar.err, 0, BCD_NEEDEXT);
     return;
   }
+  if (fwd_only) return;
   if (!tsync(p, gs, 4, 0)) return;
   if (lmax >= 1) {
     phase_bwd_deep<G, EXT>(p, p.Aoff[lmax], p.Aoff[lmax + 1], gtid, nthr);
@@ -2031,10 +2092,11 @@ __global__ void k_lists(int32_t n, const int32_t *rp, int32_t *hubs, int *nh, in
   }
 }
 __global__ void k_lists_fill(int32_t n, const int32_t *rp, const int32_t *flag, const int32_t *pos,
-                             int32_t *L, int32_t *degs) {
+                             int32_t *L, int32_t *RP, int32_t *degs) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
     if (flag[v]) {
       L[pos[v]] = v;
+      RP[pos[v]] = rp[v];
       degs[pos[v]] = rp[v + 1] - rp[v];
     }
 }
@@ -2098,13 +2160,13 @@ static void ws_release(Ctx *ctx, TileWS *ws, bool main, bool ext, bool A) {
   }
   if (main && ws->ctl) {
     void *ptrs[] = {ws->vis, ws->F, ws->ovf, ws->cand, ws->sig, ws->r, ws->Aoff, ws->Lbits, ws->HEoff,
-                    ws->C, ws->CPD, ws->Ch, ws->wsrc, ws->ctl};
+                    ws->C, ws->CPD, ws->CRP, ws->Ch, ws->wsrc, ws->ctl};
     for (void *q : ptrs) cudaFree(q);
     ctx->mem.release(nullptr, ws->bytes_main);
     ws->vis = ws->F = ws->ovf = ws->cand = nullptr;
     ws->sig = nullptr;
     ws->r = nullptr;
-    ws->Aoff = ws->HEoff = ws->C = ws->CPD = ws->Ch = nullptr;
+    ws->Aoff = ws->HEoff = ws->C = ws->CPD = ws->CRP = ws->Ch = nullptr;
     ws->Lbits = nullptr;
     ws->wsrc = nullptr;
     ws->ctl = nullptr;
@@ -2122,13 +2184,14 @@ static void ws_release(Ctx *ctx, TileWS *ws, bool main, bool ext, bool A) {
   if (A && ws->A) {
     cudaFree(ws->A);
     cudaFree(ws->ACD);
+    cudaFree(ws->ARP);
     cudaFree(ws->AM);
     cudaFree(ws->HE);
     cudaFree(ws->HEk);
     cudaFree(ws->Hdone);
     ws->HE = ws->HEk = ws->Hdone = nullptr;
     ctx->mem.release(nullptr, ws->bytes_A);
-    ws->A = ws->ACD = nullptr;
+    ws->A = ws->ACD = ws->ARP = nullptr;
     ws->AM = nullptr;
     ws->bytes_A = 0;
     ws->capA = 0;
@@ -2140,8 +2203,9 @@ static void lists_release(Ctx *ctx, TileWS *ws) {
   cudaFree(ws->hubs);
   cudaFree(ws->Lbu);
   cudaFree(ws->PDbu);
+  cudaFree(ws->RPbu);
   ctx->mem.release(nullptr, ws->bytes_lists);
-  ws->hubs = ws->Lbu = ws->PDbu = nullptr;
+  ws->hubs = ws->Lbu = ws->PDbu = ws->RPbu = nullptr;
   ws->lists_for = nullptr;
   ws->bytes_lists = 0;
 }
@@ -2164,7 +2228,7 @@ static bc_status ws_main(Ctx *ctx, TileWS *ws, int n, int T, cudaStream_t st) {
   ws_release(ctx, ws, true, true, true);
   const int G = T / 32;
   const size_t N = (size_t)n, NG = N * G, NT = N * T;
-  const size_t bytes = NG * 4 * 5 + NT * 16 + (N / 32 + 1) * 4 + (N + 3) * 4 + (N + 3) * 8 + N * 12 +
+  const size_t bytes = NG * 4 * 5 + NT * 16 + (N / 32 + 1) * 4 + (N + 3) * 4 + (N + 3) * 8 + N * 16 +
                        T * 8 + sizeof(TileCtl);
   bc_status s = ctx->mem.alloc(nullptr, bytes);
   if (s) return s;
@@ -2180,6 +2244,7 @@ static bc_status ws_main(Ctx *ctx, TileWS *ws, int n, int T, cudaStream_t st) {
   TA(ws->HEoff, (N + 3) * 4);
   TA(ws->C, N * 4);
   TA(ws->CPD, N * 4);
+  TA(ws->CRP, N * 4);
   TA(ws->Ch, N * 4);
   TA(ws->wsrc, (size_t)T * 8);
   TA(ws->ctl, sizeof(TileCtl));
@@ -2222,12 +2287,13 @@ static bc_status ws_ext(Ctx *ctx, TileWS *ws) {
 static bc_status ws_A(Ctx *ctx, TileWS *ws, int64_t cap) {
   if (ws->A && ws->capA >= cap) return BC_OK;
   ws_release(ctx, ws, false, false, true);
-  const size_t bytes = (size_t)cap * (20 + 4 * ws->G);
+  const size_t bytes = (size_t)cap * (24 + 4 * ws->G);
   bc_status s = ctx->mem.alloc(nullptr, bytes);
   if (s) return s;
   cudaError_t e = cudaSuccess;
   TA(ws->A, (size_t)cap * 4);
   TA(ws->ACD, (size_t)cap * 4);
+  TA(ws->ARP, (size_t)cap * 4);
   TA(ws->HE, (size_t)cap * 4);
   TA(ws->HEk, (size_t)cap * 4);
   TA(ws->Hdone, (size_t)cap * 4);
@@ -2235,10 +2301,10 @@ static bc_status ws_A(Ctx *ctx, TileWS *ws, int64_t cap) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     ctx->mem.release(nullptr, bytes);
-    void *ptrs[] = {ws->A, ws->ACD, ws->HE, ws->HEk, ws->Hdone, ws->AM};
+    void *ptrs[] = {ws->A, ws->ACD, ws->ARP, ws->HE, ws->HEk, ws->Hdone, ws->AM};
     for (void *q : ptrs)
       if (q) cudaFree(q);
-    ws->A = ws->ACD = ws->HE = ws->HEk = ws->Hdone = nullptr;
+    ws->A = ws->ACD = ws->ARP = ws->HE = ws->HEk = ws->Hdone = nullptr;
     ws->AM = nullptr;
     return fail(BC_ENOMEM, "tile active-list allocation failed");
   }
@@ -2275,13 +2341,14 @@ static bc_status ws_lists(Ctx *ctx, TileWS *ws, const DeviceGraph *dg, cudaStrea
   if (ws->hubs && ws->lists_for == dg->rp) return BC_OK;
   lists_release(ctx, ws);
   const size_t N = (size_t)dg->n;
-  const size_t bytes = N * 4 * 3 + 16;
+  const size_t bytes = N * 4 * 4 + 16;
   bc_status s = ctx->mem.alloc(nullptr, bytes);
   if (s) return s;
   cudaError_t e = cudaSuccess;
   TA(ws->hubs, N * 4);
   TA(ws->Lbu, N * 4);
   TA(ws->PDbu, N * 4 + 4);
+  TA(ws->RPbu, N * 4);
   int32_t *flag = nullptr, *pos = nullptr, *degs = nullptr;
   int *d_cnt = nullptr;
   void *scratch = nullptr;
@@ -2300,7 +2367,7 @@ static bc_status ws_lists(Ctx *ctx, TileWS *ws, const DeviceGraph *dg, cudaStrea
   }
   if (e == cudaSuccess) e = scan_exclusive_i32(flag, pos, (int64_t)N + 1, scratch, st);
   if (e == cudaSuccess) {
-    k_lists_fill<<<ctx->num_sms * 4, 256, 0, st>>>(dg->n, dg->rp, flag, pos, ws->Lbu, degs);
+    k_lists_fill<<<ctx->num_sms * 4, 256, 0, st>>>(dg->n, dg->rp, flag, pos, ws->Lbu, ws->RPbu, degs);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_cnt, 4, cudaMemcpyDeviceToHost, st);
@@ -2428,11 +2495,11 @@ static bc_status run_tile(Ctx *ctx, TileWS *ws, TK &p, int G, bool ext, int mode
     BC_CUDA_TRY(cudaMemcpyAsync(hc + 1, &p.ctl->lmax, 4, cudaMemcpyDeviceToHost, st));
     BC_CUDA_TRY(cudaStreamSynchronize(st));
     *lmax_out = hc[1];
-    if (fwd_only) return BC_OK;
     if (!ext && hc[0]) {
       *derr = BCD_NEEDEXT;
       return BC_OK;
     }
+    if (fwd_only) return BC_OK;
     const int lmax = hc[1];
     if (lmax >= 1) {
       s = launch(k.bdeep, grid, block, p, 0, st);
@@ -2529,6 +2596,7 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
       p.xe = ws->xe;
       p.A = ws->A;
       p.ACD = ws->ACD;
+      p.ARP = ws->ARP;
       p.AM = ws->AM;
       p.capA = ws->capA;
       p.Aoff = ws->Aoff;
@@ -2540,10 +2608,12 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
       p.Hpart = ws->Hpart;
       p.C = ws->C;
       p.CPD = ws->CPD;
+      p.CRP = ws->CRP;
       p.Ch = ws->Ch;
       p.hubs = ws->hubs;
       p.Lbu = ws->Lbu;
       p.PDbu = ws->PDbu;
+      p.RPbu = ws->RPbu;
       p.nhubs = ws->nhubs;
       p.nbu = ws->nbu;
       p.Ebu = ws->Ebu;

@@ -50,7 +50,7 @@ def test_algorithmic_bytes_model():
     import bench
     st = {"reached_vertices": 1000, "reached_arcs": 20000}
     assert bench.algorithmic_bytes(st, 1) == 8 * 20000 + 84 * 1000
-    assert bench.algorithmic_bytes(st, 64) == (8 * 20000 + 16 * 1000) / 64 + 68 * 1000
+    assert bench.algorithmic_bytes(st, 64) == (8 * 20000 + 16 * 1000) / 64 + 68 * 1000 + 1000 / 4
 
 
 def test_bench_deg2_triple_count_matches_the_selection_rule():

@@ -1,10 +1,10 @@
 """The N > 1 path of bench.py on CPU: two gloo ranks, each with its own seeded source
-shard of one replicated graph and no data-path collective.
+shard of one replicated graph, and bench.reduce_bc's sum all-reduce of the BC vector.
 
 BC is additive over sources (Alg. 1 sums the dependencies of each source independently),
 so the whole-job result of the ranks' shards is the sum of their per-shard vectors; the
 job's time is the slowest rank's (max over ranks).  The oracle stands in for the GPU
-kernels here."""
+kernels here (tests/test_gpu_multirank.py runs the library in two processes)."""
 import os
 import socket
 
@@ -38,8 +38,7 @@ def worker(rank, world, port, out_dir):
     part = oracle.bc(g, src, nthreads=1)
     fake_ms = 10.0 + 5.0 * rank  # each rank's own step time
     slowest = bench.max_over_ranks(fake_ms, dist, "cpu")
-    total = torch.from_numpy(part.copy())
-    dist.all_reduce(total)  # test-side check of additivity only; bench.py sums nothing
+    total = bench.reduce_bc(torch.from_numpy(part.copy()), dist)
     shards = [None] * world
     dist.all_gather_object(shards, src.tolist())
     if rank == 0:
@@ -68,5 +67,8 @@ def test_two_gloo_ranks_shard_sources(tmp_path):
 
 
 def test_single_rank_needs_no_process_group():
+    import torch
     import bench
     assert bench.max_over_ranks(3.5, None) == 3.5
+    v = torch.arange(4, dtype=torch.float64)
+    assert bench.reduce_bc(v, None) is v
