@@ -158,12 +158,19 @@ bc_status bc_prune(bc_graph *g, uint32_t flags, int32_t *omega, uint8_t *removed
 /* ---- autotuner ----------------------------------------------------------------------- */
 typedef struct {
   int32_t tile_width;     /* 32, 64, 128 or 256 (0 = per-source path is faster)      */
-  float alpha;            /* top-down -> bottom-up when frontier arcs > alpha * unvisited arcs */
-  float beta;             /* bottom-up -> top-down when frontier vertices < n / beta  */
+  float alpha;            /* top-down -> bottom-up when frontier arcs > alpha * unvisited
+                             arcs (tile path: > alpha * all arcs)                     */
+  float beta;             /* bottom-up -> top-down: per-source path when frontier vertices
+                             < n / beta; tile path when the frontier's arcs fall below
+                             nnz / beta (0: the alpha test decides every level)       */
   int32_t loop_mode;      /* 0 persistent kernel, 1 per-level launches, 2 CUDA graph  */
   int32_t plain_cta;      /* tile_width 0: 1 = the per-source path runs one source per
                              CTA at any size (as BC_PLAIN_CTA)                        */
   double probe_seconds;   /* time the tuner spent                                      */
+  int32_t hub_degree;     /* tile path, forward: degree from which a vertex's parents are
+                             summed by a whole CTA (load balance)                     */
+  int32_t hub_chunk;      /* tile path, backward: entries of this degree or more are split
+                             into warp work items of this many edges                  */
 } bc_tune_result;
 
 /* Time the candidate configurations on a small seeded probe of sources and cache the

@@ -67,7 +67,8 @@ class bc_stats(ctypes.Structure):
 
 class bc_tune_result(ctypes.Structure):
     _fields_ = [("tile_width", ctypes.c_int32), ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
-                ("loop_mode", ctypes.c_int32), ("plain_cta", ctypes.c_int32), ("probe_seconds", ctypes.c_double)]
+                ("loop_mode", ctypes.c_int32), ("plain_cta", ctypes.c_int32), ("probe_seconds", ctypes.c_double),
+                ("hub_degree", ctypes.c_int32), ("hub_chunk", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

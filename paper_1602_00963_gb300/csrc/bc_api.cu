@@ -179,12 +179,20 @@ bc_status run_sources(Graph *g, const int32_t *d_src, int32_t k, uint32_t flags,
   int T = 0;
   uint32_t tsel = (flags & BC_TILE_MASK) >> BC_TILE_SHIFT;
   if (tsel >= 1 && tsel <= 4) T = 32 << (tsel - 1);
-  float alpha = 0.5f, beta = 24.f;
+  float alpha = 0.5f, beta = 24.f, tile_beta = 0.f;
+  int hub = 0, hub_chunk = 0;
   int loop_mode = (flags & BC_LOOP_LAUNCH) ? 1 : (flags & BC_LOOP_GRAPH) ? 2 : 0;
   // BC_DETERMINISTIC: the autotuner's cached choice (made by timing) is not used
-  if (g->tune.ready && !(flags & BC_DETERMINISTIC)) {
+  const bool tuned = g->tune.ready && !(flags & BC_DETERMINISTIC);
+  if (tuned) {
     alpha = g->tune.res.alpha;
-    beta = g->tune.res.beta;
+    if (g->tune.res.tile_width > 0) {  // the tuned thresholds of the tile path
+      tile_beta = g->tune.res.beta;
+      hub = g->tune.res.hub_degree;
+      hub_chunk = g->tune.res.hub_chunk;
+    } else if (g->tune.res.beta > 0.f) {
+      beta = g->tune.res.beta;
+    }
     if (!tiled && !plain) {
       if (g->tune.res.tile_width > 0) {
         tiled = true;
@@ -207,7 +215,9 @@ bc_status run_sources(Graph *g, const int32_t *d_src, int32_t k, uint32_t flags,
     ta.T = T;
     ta.loop_mode = loop_mode;
     ta.alpha = alpha;
-    ta.beta = beta;
+    ta.beta = tile_beta;
+    ta.hub = hub;
+    ta.hub_chunk = hub_chunk;
     bc_status s = tile_run(ctx, g, &g->tile, ta, st, stats);
     if (s) return s;
     (void)leaf_term;
@@ -580,7 +590,7 @@ bc_status bc_sssp(bc_graph *graph, int32_t s, uint32_t flags, int32_t *depth, ui
   pa.out_ovf = d_ovf;
   pa.max_degree = g->max_degree;
   pa.alpha = g->tune.ready ? g->tune.res.alpha : 0.5f;
-  pa.beta = g->tune.ready ? g->tune.res.beta : 24.f;
+  pa.beta = (g->tune.ready && g->tune.res.tile_width == 0 && g->tune.res.beta > 0.f) ? g->tune.res.beta : 24.f;
   pa.bc = nullptr;
   if (cta) {
     r = cta_run(c, g, &g->cta, pa, st, nullptr);
@@ -638,7 +648,11 @@ bc_status bc_tile_sssp(bc_graph *graph, const int32_t *src, int32_t k, uint32_t 
   ta.T = T;
   ta.loop_mode = (flags & BC_LOOP_LAUNCH) ? 1 : (flags & BC_LOOP_GRAPH) ? 2 : 0;
   ta.alpha = g->tune.ready ? g->tune.res.alpha : 0.5f;
-  ta.beta = g->tune.ready ? g->tune.res.beta : 24.f;
+  if (g->tune.ready && g->tune.res.tile_width > 0) {
+    ta.beta = g->tune.res.beta;
+    ta.hub = g->tune.res.hub_degree;
+    ta.hub_chunk = g->tune.res.hub_chunk;
+  }
   ta.out_depth = d_dep;
   ta.out_sigma = d_sig;
   ta.out_ovf = d_ovf;

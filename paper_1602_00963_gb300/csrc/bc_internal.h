@@ -189,7 +189,9 @@ struct TileArgs {
   int32_t T;              // 32..256
   int32_t loop_mode;      // 0 persistent, 1 per-level launches, 2 CUDA graph
   float alpha;
-  float beta;
+  float beta;             // > 0: bottom-up hysteresis (see bc_tune_result); 0: alpha alone
+  int32_t hub;            // 0 = default: degree from which CTAs split an adjacency
+  int32_t hub_chunk;      // 0 = default: edges per backward hub work item
   int32_t *out_depth;     // tile sssp hook: [nsrc][n]
   unsigned long long *out_sigma;
   uint8_t *out_ovf;

@@ -293,7 +293,11 @@ void worker_main(Server *sv, int wid) {
       ta.T = T;
       ta.loop_mode = 1;
       ta.alpha = g->tune.ready ? g->tune.res.alpha : 0.2f;
-      ta.beta = 24.f;
+      if (g->tune.ready && g->tune.res.tile_width > 0) {  // the tuned tile thresholds
+        ta.beta = g->tune.res.beta;
+        ta.hub = g->tune.res.hub_degree;
+        ta.hub_chunk = g->tune.res.hub_chunk;
+      }
       ta.nreq = (int32_t)slots.size();
       ta.lane_req = job->d_lane;
       ta.req_bc = job->d_reqbc;

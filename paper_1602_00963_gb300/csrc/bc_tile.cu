@@ -30,7 +30,7 @@
 // in the prefix.  Lanes are edges for the frontier-mask tests; a hit of at most two
 // sources is loaded by its own lane, denser hits are gathered as sigma / r rows by the
 // source lanes.  Levels whose entries average at most two sources and 16 edges (high-
-// diameter graphs) run one entry per lane instead.  Vertices of degree >= kHub are
+// diameter graphs) run one entry per lane instead.  Vertices of degree >= p.hub are
 // processed by whole CTAs (forward) or as 4096-edge items spread over CTAs (backward).
 // Warp-level work is numbered across CTAs first.  σ, depth and the masks are exact.  Every
 // floating-point sum has a fixed order: an entry walked warp-wide adds its hits in edge
@@ -62,8 +62,9 @@ namespace bcl {
 namespace {
 
 constexpr int kMaxWarps = 32;       // CTA reduction scratch is sized for 1024 threads
-constexpr int kHub = 2048;          // degree from which a vertex is processed by whole CTAs
-constexpr int kHubChunk = 4096;     // edges of a hub per backward work item
+constexpr int kHubDefault = 2048;       // degree from which a vertex is processed by whole CTAs
+constexpr int kHubChunkDefault = 256;   // backward: entries of this degree or more are split
+                                        // into warp work items of this many edges
 constexpr int kLevelsPerChunk = 8;  // levels per launched chunk / captured graph
 constexpr int BCD_NEEDEXT = 4;      // device code: rerun the tile in extended mode
 
@@ -128,8 +129,9 @@ struct TileWS {
   float2 *wsrc = nullptr;
   TileCtl *ctl = nullptr;
   size_t bytes_main = 0, bytes_ext = 0, bytes_A = 0;
-  // per-graph lists: hubs (degree >= kHub) and the bottom-up walk list (others, deg > 0)
+  // per-graph lists: hubs (degree >= hub) and the bottom-up walk list (others, deg > 0)
   const int32_t *lists_for = nullptr;
+  int lists_hub = 0;  // hub degree the lists were built for
   int32_t *hubs = nullptr, *Lbu = nullptr, *PDbu = nullptr, *RPbu = nullptr;
   int nhubs = 0, nbu = 0, Ebu = 0;
   size_t bytes_lists = 0;
@@ -166,7 +168,10 @@ struct TK {
   float2 *wsrc;  // per source: omega(s) + 1, float-float
   TileCtl *ctl;
   uint32_t unused[8];
-  float alpha;
+  float alpha;  // top-down -> bottom-up when the frontier's edges exceed alpha * nnz
+  float beta;   // > 0: stay bottom-up while the frontier's edges exceed nnz / beta
+  int hub;        // degree from which a vertex is processed by whole CTAs / chunked
+  int hub_chunk;  // edges of a hub per backward work item
   uint64_t limit_ns;
   int nreq;                       // > 0: lanes route BC to per-request buffers (serving)
   const uint8_t *lane_req;        // [T] request slot of each lane
@@ -241,8 +246,8 @@ __device__ __forceinline__ void append_A(const TK &p, unsigned long long *ctr, i
       p.A[pos] = v;
       p.ACD[pos] = (int)(b & 0xffffffffull) + pre;
       p.ARP[pos] = r0;
-      if (deg >= kHub) {  // hubs are also listed for the backward sweep, one item per chunk
-        const int nch = (deg + kHubChunk - 1) / kHubChunk;
+      if (deg >= p.hub_chunk) {  // listed for the backward sweep too, one warp item per chunk
+        const int nch = (deg + p.hub_chunk - 1) / p.hub_chunk;
         const int hp = atomicAdd(&p.ctl->hecnt, nch);
         if ((long long)hp + nch <= p.capA) {
           for (int c = 0; c < nch; c++) {
@@ -310,7 +315,7 @@ __device__ __forceinline__ int find_owner(const int32_t *PD, int lo, int hi, int
 // at RP[i] = row_ptr[L[i]] and whose edges start at the level-relative prefix PD[i]; E edges
 // in all), restricted to the entries that start inside the edge range [eb, ee): ranges are
 // snapped to entry starts, so each entry is walked by exactly one warp.  With SKIP_HUBS,
-// entries of degree >= kHub are jumped over (an entry's degree is the difference of
+// entries of degree >= skip_deg are jumped over (an entry's degree is the difference of
 // consecutive prefixes, already in registers).  f(valid, k, w, col) is called once per
 // 32-edge step (lane = edge) with the warp converged: k = entry, w = its vertex, col =
 // position of the edge in col_idx.  A step's window of 32 entries is one round of
@@ -318,7 +323,7 @@ __device__ __forceinline__ int find_owner(const int32_t *PD, int lo, int hi, int
 template <bool SKIP_HUBS, typename F>
 __device__ __forceinline__ void walk_range(const TK &p, const int32_t *L, const int32_t *PD,
                                            const int32_t *RP, int i_lo, int i_hi, int E, int eb, int ee,
-                                           F &&f) {
+                                           int skip_deg, F &&f) {
   const int lane = lane_id();
   int i0 = find_owner(PD, i_lo, i_hi, eb);
   if (PD[i0] < eb) i0++;
@@ -337,7 +342,7 @@ __device__ __forceinline__ void walk_range(const TK &p, const int32_t *L, const 
     int nx = __shfl_down_sync(BC_FULL, cd, 1);
     if (lane == 31) nx = cd_after;
     if (idx + 1 >= i1) nx = e_end;
-    const unsigned hubm = SKIP_HUBS ? __ballot_sync(BC_FULL, in && nx - cd >= kHub) : 0u;
+    const unsigned hubm = SKIP_HUBS ? __ballot_sync(BC_FULL, in && nx - cd >= skip_deg) : 0u;
     if (SKIP_HUBS && (hubm & 1u)) {  // the step would start inside a hub: jump over it
       e = __shfl_sync(BC_FULL, nx, 0);
       base++;
@@ -369,7 +374,7 @@ constexpr int kChunk = 1024;
 template <bool SKIP_HUBS, typename F>
 __device__ __forceinline__ void walk(const TK &p, const int32_t *L, const int32_t *PD, const int32_t *RP,
                                      int i_lo, int i_hi, int E, int gwarp, int nwarps, unsigned long long *ctr,
-                                     F &&f) {
+                                     int skip_deg, F &&f) {
   if (E <= 0 || i_hi <= i_lo) return;
   long long ch = ((long long)E / (4ll * nwarps) + 31) & ~31ll;
   ch = ch < 32 ? 32 : (ch > kChunk ? kChunk : ch);
@@ -395,7 +400,7 @@ __device__ __forceinline__ void walk(const TK &p, const int32_t *L, const int32_
       nb = min(base0 + off, (long long)E);
       ne = min(nb + sz, (long long)E);
     }
-    walk_range<SKIP_HUBS>(p, L, PD, RP, i_lo, i_hi, E, (int)eb, (int)ee, f);
+    walk_range<SKIP_HUBS>(p, L, PD, RP, i_lo, i_hi, E, (int)eb, (int)ee, skip_deg, f);
     eb = nb;
     ee = ne;
   }
@@ -688,7 +693,7 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
   pull_init(a);
 #pragma unroll
   for (int g = 0; g < G; g++) visc[g] = 0u;
-  walk<false>(p, L, PD, RP, 0, n_list, E, gwarp, nwarps, &p.ctl->wq[level % 3],
+  walk<false>(p, L, PD, RP, 0, n_list, E, gwarp, nwarps, &p.ctl->wq[level % 3], 0,
               [&](bool valid, int k, int w, int col) {
     uint32_t vw[G];
     FwdHit<G, EXT> h;
@@ -1223,7 +1228,7 @@ __device__ void phase_mark(const TK &p, int level, int a0, int a1, int E1, int g
     }
     const int rw = isc ? p.rp[w] : 0;
     const int dw = isc ? p.rp[w + 1] - rw : 0;
-    const bool hub = isc && dw >= kHub;
+    const bool hub = isc && dw >= p.hub;
     const bool nrm = isc && !hub;
     const unsigned mn = __ballot_sync(BC_FULL, nrm), mh = __ballot_sync(BC_FULL, hub);
     if (mn) {
@@ -1342,6 +1347,7 @@ struct BwdOwner {
   int ew[EXT ? G : 1];
   float2 acc[G];   // sum of the successors' r: hits gathered as rows
   float2 accs[G];  // the same for sparse hits (at most two sources), folded in by bwd_fold
+  double bcw;      // BC[w], loaded when the owner starts (only this entry updates it this level)
 };
 
 // acc = accs + acc (a fixed order), accs = 0: the owner's full sum of the successors' r
@@ -1359,6 +1365,7 @@ __device__ __forceinline__ void bwd_fold(BwdOwner<G, EXT> &o) {
 template <int G, bool EXT>
 __device__ __forceinline__ void bwd_start(const TK &p, int w, const uint32_t (&mw)[G], BwdOwner<G, EXT> &o) {
   const int lane = lane_id();
+  o.bcw = p.nreq == 0 ? p.bc[w] : 0.0;
 #pragma unroll
   for (int g = 0; g < G; g++) {
     o.mw[g] = mw[g];
@@ -1428,12 +1435,12 @@ __device__ __forceinline__ void bwd_commit(const TK &p, int w, BwdOwner<G, EXT> 
 #pragma unroll
     for (int g = 0; g < G; g++) act |= o.mw[g];
     if (__popc(act) == 1) {  // one lane holds the whole sum
-      if (lane == __ffs(act) - 1 && !ff_zero(contrib)) p.bc[w] += ff_to(contrib);
+      if (lane == __ffs(act) - 1 && !ff_zero(contrib)) p.bc[w] = o.bcw + ff_to(contrib);
       return;
     }
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) ff_add(contrib, ff_shfl_xor(contrib, m));
-    if (lane == 0 && !ff_zero(contrib)) p.bc[w] += ff_to(contrib);
+    if (lane == 0 && !ff_zero(contrib)) p.bc[w] = o.bcw + ff_to(contrib);
     return;
   }
   // lanes belong to different requests (serving): one fixed-order sum per request
@@ -1542,7 +1549,8 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
                          int nwarps, unsigned long long *ctr) {
   int cur = -1, cur_w = -1;
   BwdOwner<G, EXT> o;
-  walk<true>(p, p.A, p.ACD, p.ARP, a0, a1, E, gwarp, nwarps, ctr, [&](bool valid, int k, int w, int col) {
+  walk<true>(p, p.A, p.ACD, p.ARP, a0, a1, E, gwarp, nwarps, ctr, p.hub_chunk,
+             [&](bool valid, int k, int w, int col) {
     BwdHit<G, EXT> h;
     h.hit = false;
     h.v = -1;
@@ -1588,21 +1596,25 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
   if (cur >= 0) bwd_commit<G, EXT>(p, cur_w, o);
 }
 
+// Backward work item i of level d's split entries (degree >= hub_chunk; one item per chunk
+// of hub_chunk edges, cut at fixed offsets from the entry's first edge): one warp sums the
+// chunk's successor terms in edge order.  A single-chunk entry is committed at once; else
+// each chunk's sum goes to the level's partial buffer and the warp finishing an entry's
+// last chunk adds the partials in chunk order (fixed, whatever the finishing order) and
+// commits.
 template <int G, bool EXT>
-__device__ void bwd_hub_item(const TK &p, int i, int h0, const uint32_t *Dn, unsigned char *smem) {
-  const int lane = lane_id(), wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ void bwd_warp_item(const TK &p, int i, int h0, const uint32_t *Dn) {
+  const int lane = lane_id();
   const int k = p.HE[i], c = p.HEk[i];
   const int w = p.A[k];
-  const int nch = (vdeg(p, w) + kHubChunk - 1) / kHubChunk;
+  const int nch = (vdeg(p, w) + p.hub_chunk - 1) / p.hub_chunk;
   BwdOwner<G, EXT> o;
   bwd_start_k<G, EXT>(p, k, o);
-  const int e0 = p.rp[w] + c * kHubChunk, e1 = min(p.rp[w + 1], e0 + kHubChunk);
-  const int per = ((e1 - e0 + nw - 1) / nw + 31) & ~31;
-  const int lo = min(e1, e0 + wid * per), hi = min(e1, lo + per);
-  for (int base = lo; base < hi; base += 32) {
+  const int e0 = p.rp[w] + c * p.hub_chunk, e1 = min(p.rp[w + 1], e0 + p.hub_chunk);
+  for (int base = e0; base < e1; base += 32) {
     const int jdx = base + lane;
     BwdHit<G, EXT> h;
-    h.v = jdx < hi ? p.ci[jdx] : -1;
+    h.v = jdx < e1 ? p.ci[jdx] : -1;
     h.hit = false;
     if (h.v >= 0) {
       load_row<G>(Dn, h.v, h.bm);
@@ -1618,47 +1630,30 @@ __device__ void bwd_hub_item(const TK &p, int i, int h0, const uint32_t *Dn, uns
     bwd_hit_load<G, EXT>(p, h);
     bwd_hits_add<G, EXT>(p, h, __ballot_sync(BC_FULL, h.sp), __ballot_sync(BC_FULL, h.hit && !h.sp), o);
   }
+  if (nch == 1) {
+    bwd_commit<G, EXT>(p, w, o);
+    return;
+  }
   bwd_fold<G, EXT>(o);
-  float2 *sa = (float2 *)smem;
-#pragma unroll 1
-  for (int g = 0; g < G; g++) {
-    __syncthreads();
-    sa[wid * 32 + lane] = o.acc[g];
-    __syncthreads();
-    if (wid == 0) {
+  float2 *part = p.Hpart + (size_t)(i - h0) * (32 * G);
+#pragma unroll
+  for (int g = 0; g < G; g++)
+    if (o.mw[g]) __stcg(&part[32 * g + lane], o.acc[g]);
+  __threadfence();
+  int last = 0;
+  if (lane == 0) last = atomicAdd(&p.Hdone[i - c], 1) == nch - 1;
+  if (__shfl_sync(BC_FULL, last, 0)) {
+    __threadfence();
+    const float2 *p0 = p.Hpart + (size_t)(i - c - h0) * (32 * G);
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      if (!o.mw[g]) continue;
       float2 sum = make_float2(0.0f, 0.0f);
-      for (int q = 0; q < nw; q++) ff_add(sum, sa[q * 32 + lane]);
+      for (int cc = 0; cc < nch; cc++) ff_add(sum, __ldcg(&p0[(size_t)cc * (32 * G) + 32 * g + lane]));
       o.acc[g] = sum;
     }
+    bwd_commit<G, EXT>(p, w, o);
   }
-  if (wid == 0) {
-    if (nch == 1) {
-      bwd_commit<G, EXT>(p, w, o);
-    } else {
-      // chunk partials of the entry; the CTA finishing its last chunk sums them in chunk
-      // order (deterministic) and commits
-      float2 *part = p.Hpart + (size_t)(i - h0) * (32 * G);
-#pragma unroll
-      for (int g = 0; g < G; g++)
-        if (o.mw[g]) __stcg(&part[32 * g + lane], o.acc[g]);
-      __threadfence();
-      int last = 0;
-      if (lane == 0) last = atomicAdd(&p.Hdone[i - c], 1) == nch - 1;
-      if (__shfl_sync(BC_FULL, last, 0)) {
-        __threadfence();
-        const float2 *p0 = p.Hpart + (size_t)(i - c - h0) * (32 * G);
-#pragma unroll
-        for (int g = 0; g < G; g++) {
-          if (!o.mw[g]) continue;
-          float2 sum = make_float2(0.0f, 0.0f);
-          for (int cc = 0; cc < nch; cc++) ff_add(sum, __ldcg(&p0[(size_t)cc * (32 * G) + 32 * g + lane]));
-          o.acc[g] = sum;
-        }
-        bwd_commit<G, EXT>(p, w, o);
-      }
-    }
-  }
-  __syncthreads();
 }
 
 // One lane-mode backward pass of vertex w for sources t0 and t1 (>= 0, or -1): r of each
@@ -1774,7 +1769,7 @@ __device__ void bwd_lanes(const TK &p, int a0, int a1, const uint32_t *Dn, int g
     int nb = 0;
 #pragma unroll
     for (int g = 0; g < G; g++) nb += __popc(mw[g]);
-    const bool hub = dg >= kHub;
+    const bool hub = dg >= p.hub_chunk;  // split into warp items
     const bool lanep = in && !hub && dg <= kLaneDeg && nb >= 1 && nb <= kLaneSrc;
     const bool fb = in && !hub && !lanep;
     if (lanep) bwd_lane_entry<G, EXT>(p, w, mw, Dn);
@@ -1834,17 +1829,17 @@ __device__ void phase_bwd_level(const TK &p, int d, int a0, int a1, int Ed, int 
     bwd_lanes<G, EXT>(p, a0, a1, Dn, gwarp, nwarps);
   else
     bwd_walk<G, EXT>(p, a0, a1, Ed, Dn, gwarp, nwarps, &p.ctl->bq[d % 3]);
-  // hub items of A_d (listed at append time, one per chunk), one per CTA from a counter
-  __shared__ int s_item;
+  // work items of A_d's split entries (listed at append time, one per chunk), one per warp
+  // from a counter, taken by each warp as soon as its walk is done
   const int h0 = p.HEoff[d], h1 = p.HEoff[d + 1];
   int *ctr = &p.ctl->bhubq[d % 3];
+  (void)smem;
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
-    __syncthreads();
-    const int i = h0 + s_item;
+    int i = 0;
+    if (lane_id() == 0) i = atomicAdd(ctr, 1);
+    i = h0 + __shfl_sync(BC_FULL, i, 0);
     if (i >= h1) break;
-    bwd_hub_item<G, EXT>(p, i, h0, Dn, smem);
+    bwd_warp_item<G, EXT>(p, i, h0, Dn);
   }
 }
 
@@ -1861,6 +1856,14 @@ __device__ void leaf_terms(const TK &p) {
 __device__ __forceinline__ int level_edges(const TK &p, int a0, int a1) {
   if (a1 <= a0) return 0;
   return p.ACD[a1 - 1] + vdeg(p, p.A[a1 - 1]);
+}
+
+// Direction of the next level from the frontier's edge count ecnt: top-down -> bottom-up
+// when ecnt > alpha * nnz; with beta > 0, a bottom-up sweep stays bottom-up while ecnt >
+// nnz / beta (hysteresis), else the alpha test decides every level.
+__device__ __forceinline__ bool next_dir(const TK &p, bool bu, int ecnt) {
+  if (bu && p.beta > 0.f) return (double)ecnt * (double)p.beta > (double)p.nnz;
+  return (double)ecnt > (double)p.alpha * (double)p.nnz;
 }
 
 // ------------------------------------------------------------------ persistent kernel
@@ -1881,8 +1884,9 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
     a_hi = (int)(pk >> 32);
     ecnt = (int)(pk & 0xffffffffull);
   }
+  bool bu = false;
   while (a_hi > a_lo) {
-    const bool bu = (double)ecnt > (double)p.alpha * (double)p.nnz;
+    bu = next_dir(p, bu, ecnt);
     phase_keep<G>(p, level, a_pp, a_lo, a_hi, gtid, nthr);
     if (!bu) {
       phase_mark<G>(p, level, a_lo, a_hi, ecnt, gwarp, nwarps);
@@ -1960,7 +1964,7 @@ __global__ void k_init_src(TK p) {
   c->a_lo = 0;
   c->a_hi = (int)(pk >> 32);
   c->ecnt = (int)(pk & 0xffffffffull);
-  c->mode = (double)c->ecnt > (double)p.alpha * (double)p.nnz;
+  c->mode = next_dir(p, false, c->ecnt);
   c->done = c->a_hi == 0;
   if (c->done) {
     c->lmax = 0;
@@ -2005,7 +2009,7 @@ __global__ void k_fwd_end(TK p) {
   c->level = level;
   p.Aoff[level] = c->a_hi;
   p.HEoff[level] = c->hecnt;
-  c->mode = (double)c->ecnt > (double)p.alpha * (double)p.nnz;
+  c->mode = next_dir(p, c->mode != 0, c->ecnt);
   if ((long long)c->a_hi > p.capA) {  // appends past the active-list capacity were dropped
     atomicCAS(&c->bar.err, 0, BCD_CAPACITY);
     c->done = 1;
@@ -2084,11 +2088,11 @@ __global__ void k_export(TK p, int lmax, int32_t *depth, unsigned long long *sig
 }
 
 // Per-graph lists: hubs, and the bottom-up walk list (non-hub vertices with an edge).
-__global__ void k_lists(int32_t n, const int32_t *rp, int32_t *hubs, int *nh, int32_t *flag) {
+__global__ void k_lists(int32_t n, const int32_t *rp, int hub, int32_t *hubs, int *nh, int32_t *flag) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const int d = rp[v + 1] - rp[v];
-    if (d >= kHub) hubs[atomicAdd(nh, 1)] = v;
-    flag[v] = (d > 0 && d < kHub) ? 1 : 0;
+    if (d >= hub) hubs[atomicAdd(nh, 1)] = v;
+    flag[v] = (d > 0 && d < hub) ? 1 : 0;
   }
 }
 __global__ void k_lists_fill(int32_t n, const int32_t *rp, const int32_t *flag, const int32_t *pos,
@@ -2313,10 +2317,11 @@ static bc_status ws_A(Ctx *ctx, TileWS *ws, int64_t cap) {
   return BC_OK;
 }
 
-// Partial sums of the backward hub chunks of one level: a level lists each hub at most
-// once, so it has at most nnz / kHubChunk + (number of hubs) items.
-static bc_status ws_hpart(Ctx *ctx, TileWS *ws, int64_t nnz) {
-  const int64_t items = nnz / kHubChunk + ws->nhubs + 16;
+// Partial sums of the backward work items of one level: a level lists each vertex at most
+// once and splits only entries of degree >= hub_chunk, so it has at most 2 nnz / hub_chunk
+// items.
+static bc_status ws_hpart(Ctx *ctx, TileWS *ws, int64_t nnz, int hub_chunk) {
+  const int64_t items = 2 * nnz / hub_chunk + 16;
   if (ws->Hpart && ws->hpart_items >= items) return BC_OK;
   if (ws->Hpart) {
     cudaFree(ws->Hpart);
@@ -2337,8 +2342,8 @@ static bc_status ws_hpart(Ctx *ctx, TileWS *ws, int64_t nnz) {
   return BC_OK;
 }
 
-static bc_status ws_lists(Ctx *ctx, TileWS *ws, const DeviceGraph *dg, cudaStream_t st) {
-  if (ws->hubs && ws->lists_for == dg->rp) return BC_OK;
+static bc_status ws_lists(Ctx *ctx, TileWS *ws, const DeviceGraph *dg, int hub, cudaStream_t st) {
+  if (ws->hubs && ws->lists_for == dg->rp && ws->lists_hub == hub) return BC_OK;
   lists_release(ctx, ws);
   const size_t N = (size_t)dg->n;
   const size_t bytes = N * 4 * 4 + 16;
@@ -2362,7 +2367,7 @@ static bc_status ws_lists(Ctx *ctx, TileWS *ws, const DeviceGraph *dg, cudaStrea
   if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, (N + 1) * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(degs, 0, (N + 1) * 4, st);
   if (e == cudaSuccess) {
-    k_lists<<<ctx->num_sms * 4, 256, 0, st>>>(dg->n, dg->rp, ws->hubs, d_cnt, flag);
+    k_lists<<<ctx->num_sms * 4, 256, 0, st>>>(dg->n, dg->rp, hub, ws->hubs, d_cnt, flag);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = scan_exclusive_i32(flag, pos, (int64_t)N + 1, scratch, st);
@@ -2392,6 +2397,7 @@ static bc_status ws_lists(Ctx *ctx, TileWS *ws, const DeviceGraph *dg, cudaStrea
   ws->nbu = h[1];
   ws->Ebu = ebu;
   ws->lists_for = dg->rp;
+  ws->lists_hub = hub;
   return BC_OK;
 }
 
@@ -2551,9 +2557,13 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
     if (!*wsp) return fail(BC_ENOMEM, "host allocation failed");
   }
   TileWS *ws = *wsp;
+  const int hub = a.hub > 0 ? a.hub : kHubDefault;
+  const int hub_chunk = a.hub_chunk > 0 ? a.hub_chunk : kHubChunkDefault;
+  if (hub < 64 || hub_chunk < 256 || hub_chunk % 32)
+    return fail(BC_EINVAL, "tile path: hub degree must be >= 64 and hub chunk a multiple of 32, >= 256");
   bc_status s = ws_main(ctx, ws, dg->n, a.T, st);
-  if (!s) s = ws_lists(ctx, ws, dg, st);
-  if (!s) s = ws_hpart(ctx, ws, dg->nnz);
+  if (!s) s = ws_lists(ctx, ws, dg, hub, st);
+  if (!s) s = ws_hpart(ctx, ws, dg->nnz, hub_chunk);
   if (s) return s;
   const int G = a.T / 32;
   if (!ws->A) {
@@ -2626,6 +2636,9 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
         p.unused[gi] = m;
       }
       p.alpha = a.alpha;
+      p.beta = a.beta;
+      p.hub = hub;
+      p.hub_chunk = hub_chunk;
       p.nreq = a.nreq;
       p.lane_req = a.lane_req ? a.lane_req + t0 : nullptr;
       p.req_bc = a.req_bc;

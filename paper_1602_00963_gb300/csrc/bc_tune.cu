@@ -1,7 +1,9 @@
 // Autotuner: times candidate configurations on a seeded probe of the graph's sources and
-// keeps the fastest (tile width, direction-switch threshold, level-loop mode, or the
-// per-source path) on the graph.  Optionally persisted in a JSON-lines cache file
-// (BC_TUNE_CACHE) keyed by GPU name and a graph signature.
+// keeps the fastest on the graph: tile width, the direction-switch thresholds (top-down ->
+// bottom-up alpha, bottom-up -> top-down beta), level-loop mode, the hub degree and hub
+// chunk of the tile path's load balance, or the per-source path (and its beta).  Optionally
+// persisted in a JSON-lines cache file (BC_TUNE_CACHE) keyed by GPU name and a graph
+// signature.
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
@@ -71,8 +73,18 @@ struct Probe {
   cudaStream_t st;
 };
 
+struct Cfg {
+  int T;            // tile width; 0 = per-source path (kernel by size), -1 = one source per CTA
+  float alpha;
+  float beta;       // tile: 0 = no hysteresis; per-source path: n / beta frontier test
+  int loop_mode;
+  int hub, chunk;   // tile path load balance
+};
+
 // seconds per source of one configuration (best of two runs)
-bc_status time_config(const Probe &pr, int T, float alpha, int loop_mode, double *sec_per_src) {
+bc_status time_config(const Probe &pr, const Cfg &c, double *sec_per_src) {
+  const int T = c.T;
+  const float alpha = c.alpha;
   double best = 1e30;
   for (int rep = 0; rep < 2; rep++) {
     bc_stats s{};
@@ -88,7 +100,7 @@ bc_status time_config(const Probe &pr, int T, float alpha, int loop_mode, double
       pa.bc = pr.d_bc;
       pa.max_degree = pr.g->max_degree;
       pa.alpha = alpha;
-      pa.beta = 24.f;
+      pa.beta = c.beta > 0.f ? c.beta : 24.f;
       if (cta) {
         r = cta_run(pr.g->ctx, pr.g, &pr.g->cta, pa, pr.st, &s);
       } else {
@@ -102,9 +114,11 @@ bc_status time_config(const Probe &pr, int T, float alpha, int loop_mode, double
       ta.nsrc = pr.k;
       ta.bc = pr.d_bc;
       ta.T = T;
-      ta.loop_mode = loop_mode;
+      ta.loop_mode = c.loop_mode;
       ta.alpha = alpha;
-      ta.beta = 24.f;
+      ta.beta = c.beta;
+      ta.hub = c.hub;
+      ta.hub_chunk = c.chunk;
       r = tile_run(pr.g->ctx, pr.g, &pr.g->tile, ta, pr.st, &s);
     }
     if (r) return r;
@@ -147,6 +161,8 @@ bool cache_lookup(const std::string &key, bc_tune_result *res) {
     if ((p = strstr(line, "\"beta\": "))) r.beta = (float)atof(p + 8);
     if ((p = strstr(line, "\"loop_mode\": "))) r.loop_mode = atoi(p + 13);
     if ((p = strstr(line, "\"plain_cta\": "))) r.plain_cta = atoi(p + 13);
+    if ((p = strstr(line, "\"hub_degree\": "))) r.hub_degree = atoi(p + 14);
+    if ((p = strstr(line, "\"hub_chunk\": "))) r.hub_chunk = atoi(p + 13);
     *res = r;
     found = true;  // the last matching line wins
   }
@@ -158,8 +174,9 @@ void cache_store(const std::string &key, const bc_tune_result &r) {
   const char *path = getenv("BC_TUNE_CACHE");
   if (!path) return;
   if (FILE *f = fopen(path, "a")) {
-    fprintf(f, "{\"key\": \"%s\", \"tile_width\": %d, \"alpha\": %.4f, \"beta\": %.2f, \"loop_mode\": %d, \"plain_cta\": %d, \"probe_seconds\": %.3f}\n",
-            key.c_str(), r.tile_width, r.alpha, r.beta, r.loop_mode, r.plain_cta, r.probe_seconds);
+    fprintf(f, "{\"key\": \"%s\", \"tile_width\": %d, \"alpha\": %.4f, \"beta\": %.2f, \"loop_mode\": %d, \"plain_cta\": %d, \"hub_degree\": %d, \"hub_chunk\": %d, \"probe_seconds\": %.3f}\n",
+            key.c_str(), r.tile_width, r.alpha, r.beta, r.loop_mode, r.plain_cta, r.hub_degree, r.hub_chunk,
+            r.probe_seconds);
     fclose(f);
   }
 }
@@ -217,45 +234,61 @@ extern "C" bc_status bc_autotune(bc_graph *graph, int32_t probe_sources, uint64_
     return cuda_fail(ce, "bc_autotune: copy of the probe sources");
   }
   double best = 1e30, t;
-  int bestT = 64, bestMode = 0;
-  float bestA = 0.2f;
+  Cfg cur{64, 0.2f, 0.f, 0, 2048, 256};
+  // a later stage's value replaces the current one only when it is clearly faster (2%):
+  // timing noise must not pick a threshold
+  auto stage = [&](auto set, std::initializer_list<double> vals, double margin) {
+    for (double v : vals) {
+      if (s) return;
+      Cfg c = cur;
+      set(c, v);
+      s = time_config(pr, c, &t);
+      if (!s && t < best * margin) best = t, cur = c;
+    }
+  };
   // stage 1: tile width
-  for (int T : {32, 64, 128, 256}) {
-    s = time_config(pr, T, bestA, 0, &t);
-    if (s) break;
-    if (t < best) best = t, bestT = T;
-  }
-  // stage 2: bottom-up switch threshold of the tile path
-  for (float a : {0.02f, 0.05f, 0.5f, 2.0f}) {
-    if (s) break;
-    s = time_config(pr, bestT, a, 0, &t);
-    if (!s && t < best) best = t, bestA = a;
-  }
+  stage([](Cfg &c, double v) { c.T = (int)v; }, {32, 64, 128, 256}, 1.0);
+  // stage 2: top-down -> bottom-up threshold of the tile path
+  stage([](Cfg &c, double v) { c.alpha = (float)v; }, {0.02, 0.05, 0.5, 2.0}, 1.0);
   // stage 3: level-loop mode (matters on long-diameter graphs)
-  for (int m : {1, 2}) {
-    if (s) break;
-    s = time_config(pr, bestT, bestA, m, &t);
-    if (!s && t < best * 0.97) best = t, bestMode = m;
-  }
-  // stage 4: the per-source path (the kernel chosen by size, and on larger graphs also one
-  // source per CTA, which suits sparse high-diameter graphs)
+  stage([](Cfg &c, double v) { c.loop_mode = (int)v; }, {1, 2}, 0.97);
+  // stage 4: bottom-up -> top-down hysteresis (0 = none)
+  stage([](Cfg &c, double v) { c.beta = (float)v; }, {4, 16}, 0.98);
+  // stage 5: load balance of high-degree vertices (forward: degree pulled by whole CTAs;
+  // backward: edges per warp work item of a split entry)
+  stage([](Cfg &c, double v) { c.hub = (int)v; }, {1024, 4096}, 0.98);
+  stage([](Cfg &c, double v) { c.chunk = (int)v; }, {512, 1024}, 0.98);
+  // stage 6: the per-source path (the kernel chosen by size, and on larger graphs also one
+  // source per CTA, which suits sparse high-diameter graphs); the grid-wide kernel's beta
   double tplain = 1e30, tcta = 1e30;
-  if (!s) s = time_config(pr, 0, 0.5f, 0, &tplain);
-  if (!s && !cta_fits(g->g.n) && g->g.n <= kCtaForcedMaxN) s = time_config(pr, -1, 0.5f, 0, &tcta);
+  float pbeta = 24.f;
+  if (!s) s = time_config(pr, Cfg{0, 0.5f, 24.f, 0, 0, 0}, &tplain);
+  const bool grid_kernel = !cta_fits(g->g.n);
+  if (!s && grid_kernel && tplain < best) {
+    for (float b : {8.f, 64.f}) {
+      if (s) break;
+      s = time_config(pr, Cfg{0, 0.5f, b, 0, 0, 0}, &t);
+      if (!s && t < tplain * 0.98) tplain = t, pbeta = b;
+    }
+  }
+  if (!s && grid_kernel && g->g.n <= kCtaForcedMaxN) s = time_config(pr, Cfg{-1, 0.5f, 24.f, 0, 0, 0}, &tcta);
   c->mem.release(pr.d_src, hs.size() * 4 + 4);
   c->mem.release(pr.d_bc, (size_t)g->g.n * 8);
   if (s) return s;
   if (std::min(tplain, tcta) < best) {
     res.tile_width = 0;
     res.alpha = 0.5f;
+    res.beta = pbeta;
     res.loop_mode = 0;
     res.plain_cta = tcta < tplain ? 1 : 0;
   } else {
-    res.tile_width = bestT;
-    res.alpha = bestA;
-    res.loop_mode = bestMode;
+    res.tile_width = cur.T;
+    res.alpha = cur.alpha;
+    res.beta = cur.beta;
+    res.loop_mode = cur.loop_mode;
+    res.hub_degree = cur.hub;
+    res.hub_chunk = cur.chunk;
   }
-  res.beta = 24.f;
   res.probe_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   g->tune.res = res;
   g->tune.ready = true;

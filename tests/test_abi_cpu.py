@@ -73,7 +73,7 @@ def test_code_hash_ignores_comments_only(tmp_path):
     a = tmp_path / "a.cu"
     a.write_text(text.replace("// Warp-level work is numbered", "// Warp work is numbered"))
     b = tmp_path / "b.cu"
-    b.write_text(text.replace("constexpr int kHub = 2048;", "constexpr int kHub = 2049;"))
+    b.write_text(text.replace("constexpr int kHubDefault = 2048;", "constexpr int kHubDefault = 2049;"))
     assert bench.code_sha1(str(a)) == bench.code_sha1(src) != bench.code_sha1(str(b))
 
 
