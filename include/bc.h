@@ -167,8 +167,9 @@ typedef struct {
   int32_t plain_cta;      /* tile_width 0: 1 = the per-source path runs one source per
                              CTA at any size (as BC_PLAIN_CTA)                        */
   double probe_seconds;   /* time the tuner spent                                      */
-  int32_t hub_degree;     /* tile path, forward: degree from which a vertex's parents are
-                             summed by a whole CTA (load balance)                     */
+  int32_t hub_degree;     /* tile path, forward: candidates of this degree or more have
+                             their parents summed in warp work items of hub_chunk edges
+                             (load balance)                                           */
   int32_t hub_chunk;      /* tile path, backward: entries of this degree or more are split
                              into warp work items of this many edges                  */
 } bc_tune_result;

@@ -30,12 +30,15 @@
 // in the prefix.  Lanes are edges for the frontier-mask tests; a hit of at most two
 // sources is loaded by its own lane, denser hits are gathered as sigma / r rows by the
 // source lanes.  Levels whose entries average at most two sources and 16 edges (high-
-// diameter graphs) run one entry per lane instead.  Vertices of degree >= p.hub are
-// processed by whole CTAs (forward) or as 4096-edge items spread over CTAs (backward).
+// diameter graphs) run one entry per lane instead.  High-degree vertices are cut into
+// chunks of p.hub_chunk edges at fixed offsets (forward candidates of degree >= p.hub,
+// backward entries of degree >= p.hub_chunk), each a warp work item taken from a counter
+// as soon as a warp's walk is done; the warp finishing a vertex's last chunk adds the
+// chunks' partial sums in chunk order and commits.
 // Warp-level work is numbered across CTAs first.  σ, depth and the masks are exact.  Every
 // floating-point sum has a fixed order: an entry walked warp-wide adds its hits in edge
 // order (wherever the warps' run-time range claims put the 32-edge steps), the lane-per-
-// entry mode walks an entry's edges in order, hub items split an adjacency at fixed
+// entry mode walks an entry's edges in order, work items split an adjacency at fixed
 // offsets and their partials are summed in chunk order, and BC takes one update per
 // (vertex, level) in level order.  So r and BC repeat bit for bit from run to run.
 //
@@ -50,7 +53,6 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "bc_ff.cuh"
@@ -61,8 +63,8 @@ namespace bcl {
 
 namespace {
 
-constexpr int kMaxWarps = 32;       // CTA reduction scratch is sized for 1024 threads
-constexpr int kHubDefault = 2048;       // degree from which a vertex is processed by whole CTAs
+constexpr int kHubDefault = 512;        // forward: candidates of this degree or more are split
+                                        // into warp work items (below)
 constexpr int kHubChunkDefault = 256;   // backward: entries of this degree or more are split
                                         // into warp work items of this many edges
 constexpr int kLevelsPerChunk = 8;  // levels per launched chunk / captured graph
@@ -83,7 +85,7 @@ struct TileCtl {
   GridSync bar;
   unsigned long long apack[3];  // per-level append counter of A: count << 32 | edges (slot l % 3)
   unsigned long long cpack[3];  // per-level candidates C: count << 32 | edges (slot l % 3)
-  int chcnt[3];                 // per-level hub candidates (slot l % 3)
+  unsigned long long chpk[3];   // per-level hub candidates: count << 32 | chunks (slot l % 3)
   int hecnt;                    // hub entries listed in HE
   int hubq[3];                  // forward hub work counter (slot l % 3)
   int bhubq[3];                 // backward hub work counter (slot d % 3)
@@ -100,9 +102,6 @@ struct TileCtl {
   unsigned long long reached_arcs;  // their adjacency entries
   unsigned long long ns[256];   // Eq. 3 component size per lane (leaf term)
 };
-
-// shared-memory scratch of the CTA reductions (hubs)
-constexpr size_t kSmemTile = (size_t)kMaxWarps * 32 * (8 + 8 + 4 + 4) + kMaxWarps * 4 + 64;
 
 }  // namespace
 
@@ -123,17 +122,21 @@ struct TileWS {
   int32_t *HE = nullptr, *HEoff = nullptr;  // hub work items (A positions), per-level offsets
   int32_t *HEk = nullptr, *Hdone = nullptr;  // item's chunk number; chunks done per hub entry
   float2 *Hpart = nullptr;                   // per-item partial sums (one level's items)
-  int64_t hpart_items = 0;
-  size_t bytes_hpart = 0;
-  int32_t *C = nullptr, *CPD = nullptr, *CRP = nullptr, *Ch = nullptr;
+  uint32_t *FPm = nullptr;                   // forward items: masks and overflow bits
+  double *FPx = nullptr;                     // forward items, extended range
+  int32_t *FPe = nullptr;
+  int64_t hpart_items = 0, hpart_ext_items = 0;
+  size_t bytes_hpart = 0, bytes_hpart_ext = 0;
+  int32_t *C = nullptr, *CPD = nullptr, *CRP = nullptr, *Ch = nullptr, *ChP = nullptr;
+  int32_t *Fdone = nullptr;  // forward: finished chunks per split candidate
   float2 *wsrc = nullptr;
   TileCtl *ctl = nullptr;
   size_t bytes_main = 0, bytes_ext = 0, bytes_A = 0;
   // per-graph lists: hubs (degree >= hub) and the bottom-up walk list (others, deg > 0)
   const int32_t *lists_for = nullptr;
-  int lists_hub = 0;  // hub degree the lists were built for
-  int32_t *hubs = nullptr, *Lbu = nullptr, *PDbu = nullptr, *RPbu = nullptr;
-  int nhubs = 0, nbu = 0, Ebu = 0;
+  int lists_hub = 0, lists_chunk = 0;  // hub degree and chunk the lists were built for
+  int32_t *hubs = nullptr, *Lbu = nullptr, *PDbu = nullptr, *RPbu = nullptr, *HPbu = nullptr;
+  int nhubs = 0, nbu = 0, Ebu = 0, nhub_items = 0;
   size_t bytes_lists = 0;
 };
 
@@ -162,7 +165,14 @@ struct TK {
   int32_t *HE, *HEoff;
   int32_t *HEk, *Hdone;  // backward hub items: chunk number; finished chunks of the entry
   float2 *Hpart;         // [items of a level][T] partial r sums of hub chunks
-  int32_t *C, *CPD, *CRP, *Ch;
+  unsigned long long *FPs;  // forward items: [items][T] partial sigma sums (shares Hpart)
+  uint32_t *FPm;            // forward items: [items][2G] new-level masks, overflow bits
+  double *FPx;              // forward items, extended range: [items][T] mantissas
+  int32_t *FPe;             //   and exponents
+  int32_t *Fdone;           // forward: finished chunks per split candidate (list position)
+  const int32_t *HPbu;      // bottom-up: exclusive prefix of the hubs' chunk counts
+  int nhub_items;           // bottom-up: items of all hubs
+  int32_t *C, *CPD, *CRP, *Ch, *ChP;
   const int32_t *hubs, *Lbu, *PDbu, *RPbu;
   int nhubs, nbu, Ebu;
   float2 *wsrc;  // per source: omega(s) + 1, float-float
@@ -205,6 +215,46 @@ __device__ __forceinline__ int vdeg(const TK &p, int v) { return p.rp[v + 1] - p
 // Warp index for warp-level work, interleaved across CTAs (warp i of every CTA before warp
 // i + 1 of any), so that a level with few work units still spreads over all SMs.
 __device__ __forceinline__ int warp_rank() { return (int)((threadIdx.x >> 5) * gridDim.x + blockIdx.x); }
+// Position of source t = 32 g + lane in vertex v's row of a per-(vertex, source) array
+// ([n][T]: sigma, r, the extended-range arrays): a lane's G sources are adjacent, so a lane
+// reads all of its sources of a row with vector loads.
+template <int G>
+__device__ __forceinline__ size_t sidx(long long v, int g, int lane) {
+  return (size_t)v * (32 * G) + (size_t)lane * G + g;
+}
+template <int G>
+__device__ __forceinline__ size_t sidx(long long v, int t) {
+  return sidx<G>(v, t >> 5, t & 31);
+}
+
+// A lane's G adjacent values of a row (a = row + lane * G), in 16-byte vector loads.
+template <int G>
+__device__ __forceinline__ void load_lane(const unsigned long long *a, unsigned long long (&out)[G]) {
+  if constexpr (G == 1) {
+    out[0] = a[0];
+  } else {
+#pragma unroll
+    for (int q = 0; q < G / 2; q++) {
+      const ulonglong2 x = ((const ulonglong2 *)a)[q];
+      out[2 * q] = x.x;
+      out[2 * q + 1] = x.y;
+    }
+  }
+}
+template <int G>
+__device__ __forceinline__ void load_lane(const float2 *a, float2 (&out)[G]) {
+  if constexpr (G == 1) {
+    out[0] = a[0];
+  } else {
+#pragma unroll
+    for (int q = 0; q < G / 2; q++) {
+      const float4 x = ((const float4 *)a)[q];
+      out[2 * q] = make_float2(x.x, x.y);
+      out[2 * q + 1] = make_float2(x.z, x.w);
+    }
+  }
+}
+
 // Row v of a [n][G] mask array in one or two vector loads (rows are 4G-byte aligned).
 template <int G>
 __device__ __forceinline__ void load_row(const uint32_t *a, long long v, uint32_t (&out)[G]) {
@@ -438,7 +488,7 @@ __device__ __forceinline__ void pull_hit(const TK &p, int pn, const uint32_t (&m
   for (int g = 0; g < G; g++) {
     a.newm[g] |= m[g];
     if ((m[g] >> lane) & 1u) {
-      const size_t idx = (size_t)pn * (32 * G) + 32 * g + lane;
+      const size_t idx = sidx<G>(pn, g, lane);
       const unsigned long long sv = p.sig[idx];
       const unsigned long long old = a.s[g];
       a.s[g] = old + sv;
@@ -476,7 +526,7 @@ __device__ __forceinline__ bool pull_commit(const TK &p, int w, int level, const
     any = true;
     const bool mine = (m >> lane) & 1u;
     const bool og = (a.o >> g) & 1u;
-    const size_t idx = (size_t)w * (32 * G) + 32 * g + lane;
+    const size_t idx = sidx<G>(w, g, lane);
     if (mine) {
       p.sig[idx] = a.s[g];
       if (EXT && og) {
@@ -573,10 +623,10 @@ __device__ __forceinline__ void fwd_hit_load(const TK &p, FwdHit<G, EXT> &h) {
   h.x0.m = h.x1.m = 0.0;
   h.x0.e = h.x1.e = 0;
   if (!h.sp) return;
-  const size_t i0 = (size_t)h.pj * (32 * G) + h.t0;
+  const size_t i0 = sidx<G>(h.pj, h.t0);
   h.s0 = p.sig[i0];
   h.o0 = EXT && ((p.ovf[(size_t)h.pj * G + (h.t0 >> 5)] >> (h.t0 & 31)) & 1u);
-  const size_t i1 = (size_t)h.pj * (32 * G) + (h.t1 >= 0 ? h.t1 : h.t0);
+  const size_t i1 = sidx<G>(h.pj, (h.t1 >= 0 ? h.t1 : h.t0));
   if (h.t1 >= 0) {
     h.s1 = p.sig[i1];
     h.o1 = EXT && ((p.ovf[(size_t)h.pj * G + (h.t1 >> 5)] >> (h.t1 & 31)) & 1u);
@@ -658,11 +708,21 @@ __device__ __forceinline__ void fwd_hits_add(const TK &p, const FwdHit<G, EXT> &
       const int jq = hd ? __ffs(hd) - 1 : -1;
       if (hd) hd &= hd - 1;
       const int pn = __shfl_sync(BC_FULL, h.pj, jq < 0 ? 0 : jq);
+      bool mine = false;
 #pragma unroll
       for (int g = 0; g < G; g++) {
         const uint32_t m = __shfl_sync(BC_FULL, h.bm[g], jq < 0 ? 0 : jq);
         mq[q][g] = jq < 0 ? 0u : m;
-        sv[q][g] = ((mq[q][g] >> lane) & 1u) ? p.sig[(size_t)pn * (32 * G) + 32 * g + lane] : 0ull;
+        mine |= (mq[q][g] >> lane) & 1u;
+      }
+      if (mine) {  // the lane's G values of the row in vector loads
+        load_lane<G>(p.sig + sidx<G>(pn, 0, lane), sv[q]);
+#pragma unroll
+        for (int g = 0; g < G; g++)
+          if (!((mq[q][g] >> lane) & 1u)) sv[q][g] = 0ull;
+      } else {
+#pragma unroll
+        for (int g = 0; g < G; g++) sv[q][g] = 0ull;
       }
     }
 #pragma unroll
@@ -745,25 +805,32 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
     abuf_push(p, ab, cur, ap, a_base);
 }
 
-// Whole-CTA pull of a hub: warps take contiguous slices of the adjacency; warp 0 folds
-// the partial sums in warp order (deterministic) and commits.  Returns (in warp 0)
-// whether any lane reached w.
+// Forward work item i of level l's split candidates (degree >= p.hub; list L with the
+// exclusive prefix IP of their chunk counts, nl entries; one item per chunk of p.hub_chunk
+// edges at fixed offsets from the vertex's first edge): one warp sums, per source lane,
+// sigma over the chunk's parents.  A single-chunk vertex is committed at once; otherwise the
+// chunk's sums, new-level masks and overflow bits go to the level's partial buffers and the
+// warp finishing the vertex's last chunk adds them up in chunk order (a fixed order, so the
+// extended-range sums repeat bit for bit) and commits.
 template <int G, bool EXT>
-__device__ bool pull_hub_cta(const TK &p, int w, int level, bool leaf,
-                             unsigned long long (&nsacc)[G], unsigned char *smem) {
-  const int lane = lane_id(), wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ void fwd_warp_item(const TK &p, int level, const int32_t *L, const int32_t *IP, int nl, int i,
+                              unsigned long long *ap, int a_base, bool leaf, unsigned long long (&nsacc)[G]) {
+  const int lane = lane_id();
+  const int k = find_owner(IP, 0, nl, i);
+  const int c = i - IP[k];
+  const int w = L[k];
   uint32_t visw[G];
-  if (load_vis<G>(p, w, visw)) return false;  // same for every thread of the CTA
+  if (load_vis<G>(p, w, visw)) return;  // reached by every source: none of w's items commits
+  const int r0 = p.rp[w], r1 = p.rp[w + 1];
+  const int nch = (r1 - r0 + p.hub_chunk - 1) / p.hub_chunk;
+  const int e0 = r0 + c * p.hub_chunk, e1 = min(r1, e0 + p.hub_chunk);
+  const uint32_t *Fp = Fbuf<G>(p, level - 1);
   PullAcc<G, EXT> a;
   pull_init(a);
-  const uint32_t *Fp = Fbuf<G>(p, level - 1);
-  const int e0 = p.rp[w], e1 = p.rp[w + 1];
-  const int per = ((e1 - e0 + nw - 1) / nw + 31) & ~31;
-  const int lo = min(e1, e0 + wid * per), hi = min(e1, lo + per);
-  for (int base = lo; base < hi; base += 32) {
+  for (int base = e0; base < e1; base += 32) {
     const int jdx = base + lane;
     FwdHit<G, EXT> h;
-    h.pj = jdx < hi ? p.ci[jdx] : -1;
+    h.pj = jdx < e1 ? p.ci[jdx] : -1;
     h.hit = false;
     if (h.pj >= 0) {
       load_row<G>(Fp, h.pj, h.bm);
@@ -779,51 +846,50 @@ __device__ bool pull_hub_cta(const TK &p, int w, int level, bool leaf,
     fwd_hit_load<G, EXT>(p, h);
     fwd_hits_add<G, EXT>(p, h, __ballot_sync(BC_FULL, h.sp), __ballot_sync(BC_FULL, h.hit && !h.sp), a);
   }
-  unsigned long long *ss = (unsigned long long *)smem;  // [32 warps][32]
-  double *sxm = (double *)(ss + kMaxWarps * 32);       // [32][32]
-  uint32_t *so = (uint32_t *)(sxm + kMaxWarps * 32);    // [32][32]
-  int *sxe = (int *)(so + kMaxWarps * 32);              // [32][32]
-  uint32_t *sm = (uint32_t *)(sxe + kMaxWarps * 32);    // [32]
-#pragma unroll 1
-  for (int g = 0; g < G; g++) {
-    __syncthreads();
-    ss[wid * 32 + lane] = a.s[g];
-    so[wid * 32 + lane] = (a.o >> g) & 1u;
-    if (lane == 0) sm[wid] = a.newm[g];
-    if (EXT) {
-      sxm[wid * 32 + lane] = a.x[g].m;
-      sxe[wid * 32 + lane] = a.x[g].e;
+  if (nch > 1) {
+    unsigned long long *ps = p.FPs + (size_t)i * (32 * G);
+    uint32_t *pm = p.FPm + (size_t)i * (2 * G);
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      __stcg(&ps[32 * g + lane], a.s[g]);
+      const unsigned ob = __ballot_sync(BC_FULL, (a.o >> g) & 1u);
+      if (lane == 0) {
+        __stcg(&pm[g], a.newm[g]);
+        __stcg(&pm[G + g], ob);
+      }
+      if (EXT) {
+        __stcg(&p.FPx[(size_t)i * (32 * G) + 32 * g + lane], a.x[g].m);
+        __stcg(&p.FPe[(size_t)i * (32 * G) + 32 * g + lane], a.x[g].e);
+      }
     }
-    __syncthreads();
-    if (wid == 0) {
-      unsigned long long s = 0ull;
-      bool o = false;
-      uint32_t m = 0u;
-      XS x;
-      x.m = 0.0;
-      x.e = 0;
-      for (int k = 0; k < nw; k++) {
-        const unsigned long long old = s;
-        s += ss[k * 32 + lane];
-        o |= (s < old) || so[k * 32 + lane] != 0u;
-        m |= sm[k];
+    __threadfence();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(&p.Fdone[k], 1) == nch - 1;
+    if (!__shfl_sync(BC_FULL, last, 0)) return;
+    __threadfence();
+    pull_init(a);
+    for (int cc = 0; cc < nch; cc++) {
+      const size_t it = (size_t)(i - c + cc);
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        const unsigned long long v = __ldcg(&p.FPs[it * (32 * G) + 32 * g + lane]);
+        const unsigned long long old = a.s[g];
+        a.s[g] = old + v;
+        const uint32_t ob = __ldcg(&p.FPm[it * (2 * G) + G + g]);
+        if (a.s[g] < old || ((ob >> lane) & 1u)) a.o |= 1u << g;
+        a.newm[g] |= __ldcg(&p.FPm[it * (2 * G) + g]);
         if (EXT) {
           XS y;
-          y.m = sxm[k * 32 + lane];
-          y.e = sxe[k * 32 + lane];
-          xs_add(x, y);
+          y.m = __ldcg(&p.FPx[it * (32 * G) + 32 * g + lane]);
+          y.e = __ldcg(&p.FPe[it * (32 * G) + 32 * g + lane]);
+          xs_add(a.x[g], y);
         }
       }
-      a.s[g] = s;
-      a.o = (a.o & ~(1u << g)) | ((o ? 1u : 0u) << g);
-      a.newm[g] = m;
-      if (EXT) a.x[g] = x;
     }
+    if (lane == 0) p.Fdone[k] = 0;  // clean for the next level
   }
-  bool any = false;
-  if (wid == 0) any = pull_commit<G, EXT>(p, w, level, a, visw, leaf, nsacc);
-  __syncthreads();
-  return any;
+  const bool any = pull_commit<G, EXT>(p, w, level, a, visw, leaf, nsacc);
+  append_A(p, ap, a_base, any && lane == 0, w);
 }
 
 // ------------------------------------------------------------------ lane-per-entry mode
@@ -899,7 +965,7 @@ __device__ __forceinline__ void lane_pull(const TK &p, const uint32_t *Fp, int w
           const int bit = __ffs(m) - 1;
           m &= m - 1;
           const int t = 32 * g + bit;
-          const size_t idx = (size_t)pj[u] * (32 * G) + t;
+          const size_t idx = sidx<G>(pj[u], t);
           const unsigned long long v = p.sig[idx];
           const bool po = EXT && ((p.ovf[(size_t)pj[u] * G + g] >> bit) & 1u);
           XS x;
@@ -949,7 +1015,7 @@ __device__ __forceinline__ void lane_pull_pair(const TK &p, const uint32_t *Fp, 
         LaneSlot<EXT> &sl = z ? b : a;
         const uint32_t f = z ? fb[u] : fa[u];
         if (sl.t < 0 || !((f >> (sl.t & 31)) & 1u)) continue;
-        const size_t idx = (size_t)pj[u] * (32 * G) + sl.t;
+        const size_t idx = sidx<G>(pj[u], sl.t);
         const unsigned long long v = p.sig[idx];
         const bool po = EXT && ((p.ovf[(size_t)pj[u] * G + (sl.t >> 5)] >> (sl.t & 31)) & 1u);
         XS x;
@@ -975,7 +1041,7 @@ template <int G, bool EXT>
 __device__ __forceinline__ void lane_store_slot(const TK &p, int w, const LaneSlot<EXT> &z, uint32_t (&nm)[G],
                                                 uint32_t (&om)[G], bool leaf) {
   if (z.t < 0) return;
-  const size_t idx = (size_t)w * (32 * G) + z.t;
+  const size_t idx = sidx<G>(w, z.t);
   p.sig[idx] = z.s;
   if (EXT && z.o) {
     const XS x = xs_norm(z.x);
@@ -1132,7 +1198,7 @@ __device__ void init_sources(const TK &p) {
     bool first = true;
     for (int h = 0; h < G; h++) first &= (p.vis[(size_t)s * G + h] & ~p.unused[h]) == 0u;
     p.vis[(size_t)s * G + g] |= bit;
-    p.sig[(size_t)s * (32 * G) + t] = 1ull;
+    p.sig[sidx<G>(s, t)] = 1ull;
     if (ds > 0) {
       F0[(size_t)s * G + g] |= bit;
       if (first) {
@@ -1148,7 +1214,7 @@ __device__ void init_sources(const TK &p) {
   p.ctl->apack[0] = pack_qe(cnt, edges);
   p.ctl->apack[1] = p.ctl->apack[2] = 0ull;
   p.ctl->cpack[0] = p.ctl->cpack[1] = p.ctl->cpack[2] = 0ull;
-  p.ctl->chcnt[0] = p.ctl->chcnt[1] = p.ctl->chcnt[2] = 0;
+  p.ctl->chpk[0] = p.ctl->chpk[1] = p.ctl->chpk[2] = 0ull;
   p.Aoff[0] = 0;
   p.Lbits[0] = 0ull;
   p.HEoff[0] = 0;
@@ -1199,7 +1265,7 @@ __device__ void phase_mark(const TK &p, int level, int a0, int a1, int E1, int g
   const uint32_t *Fp = Fbuf<G>(p, level - 1);
   int base = find_owner(p.ACD, a0, a1, (int)eb);
   unsigned long long *cp = &p.ctl->cpack[level % 3];
-  int *chp = &p.ctl->chcnt[level % 3];
+  unsigned long long *chp = &p.ctl->chpk[level % 3];
   for (int e = (int)eb; e < ee; e += 32) {
     const int idx = base + lane;
     const bool in = idx < a1;
@@ -1244,11 +1310,18 @@ __device__ void phase_mark(const TK &p, int level, int a0, int a1, int E1, int g
         p.CRP[pos] = rw;
       }
     }
-    if (mh) {
-      int b = 0;
-      if (lane == 0) b = atomicAdd(chp, __popc(mh));
+    if (mh) {  // split candidates, with the exclusive prefix of their chunk counts
+      const int nchk = hub ? (dw + p.hub_chunk - 1) / p.hub_chunk : 0;
+      int tot;
+      const int pre = warp_excl_scan(nchk, &tot);
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(chp, pack_qe(__popc(mh), (unsigned)tot));
       b = __shfl_sync(BC_FULL, b, 0);
-      if (hub) p.Ch[b + __popc(mh & lanemask_lt())] = w;
+      if (hub) {
+        const int pos = (int)(b >> 32) + __popc(mh & lanemask_lt());
+        p.Ch[pos] = w;
+        p.ChP[pos] = (int)(b & 0xffffffffull) + pre;
+      }
     }
     const int j31 = __shfl_sync(BC_FULL, j, 31);
     int nxt = __shfl_sync(BC_FULL, cdj, min(j31 + 1, 31));
@@ -1260,16 +1333,18 @@ __device__ void phase_mark(const TK &p, int level, int a0, int a1, int E1, int g
 // Pull of level l: hubs (Ch, or every hub in bottom-up mode) by whole CTAs, then the walk
 // over C (top-down) or over every non-hub vertex (bottom-up).  Reached vertices go to A_l.
 template <int G, bool EXT>
-__device__ void phase_pull(const TK &p, int level, bool bu, int a_lo, int a_base, int gwarp, int nwarps,
-                           unsigned char *smem) {
+__device__ void phase_pull(const TK &p, int level, bool bu, int a_lo, int a_base, int gwarp, int nwarps) {
   const int lane = lane_id();
   const bool leaf = p.leaf_term && p.omega;
   unsigned long long nsacc[G];
 #pragma unroll
   for (int g = 0; g < G; g++) nsacc[g] = 0ull;
   unsigned long long *ap = &p.ctl->apack[level % 3];
-  const int nh = bu ? p.nhubs : *(volatile int *)&p.ctl->chcnt[level % 3];
+  const unsigned long long chk = vload64(&p.ctl->chpk[level % 3]);
+  const int nh = bu ? p.nhubs : (int)(chk >> 32);
+  const int nitems = bu ? p.nhub_items : (int)(chk & 0xffffffffull);
   const int32_t *hl = bu ? p.hubs : p.Ch;
+  const int32_t *hp = bu ? p.HPbu : p.ChP;
   AppendBuf ab;
   ab.v = 0;
   ab.n = 0;
@@ -1296,18 +1371,14 @@ __device__ void phase_pull(const TK &p, int level, bool bu, int a_lo, int a_base
     }
   }
   abuf_flush(p, ab, ap, a_base);
-  // hubs last, taken from a shared work counter so that CTAs done with their walk share
-  // pick them up (balances the few, very large adjacency lists)
-  __shared__ int s_item;
+  // work items of the split candidates, one per warp from a counter, taken by each warp as
+  // soon as its walk is done (balances the few, very large adjacency lists)
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_item = atomicAdd(&p.ctl->hubq[level % 3], 1);
-    __syncthreads();
-    const int i = s_item;
-    if (i >= nh) break;
-    const int w = hl[i];
-    const bool any = pull_hub_cta<G, EXT>(p, w, level, leaf, nsacc, smem);
-    if ((threadIdx.x >> 5) == 0) append_A(p, ap, a_base, any && lane == 0, w);
+    int i = 0;
+    if (lane == 0) i = atomicAdd(&p.ctl->hubq[level % 3], 1);
+    i = __shfl_sync(BC_FULL, i, 0);
+    if (i >= nitems) break;
+    fwd_warp_item<G, EXT>(p, level, hl, hp, nh, i, ap, a_base, leaf, nsacc);
   }
   if (leaf) {
 #pragma unroll
@@ -1326,7 +1397,7 @@ __device__ void phase_bwd_deep(const TK &p, int a0, int a1, int gtid, int nthr) 
     if (!((m >> ln) & 1u)) continue;
     const int w = p.A[k];
     const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
-    const size_t idx = (size_t)w * (32 * G) + t;
+    const size_t idx = sidx<G>(w, t);
     float2 sg;
     if (EXT) {
       const bool o = (p.ovf[(size_t)w * G + g] >> ln) & 1u;
@@ -1343,7 +1414,8 @@ __device__ void phase_bwd_deep(const TK &p, int a0, int a1, int gtid, int nthr) 
 template <int G, bool EXT>
 struct BwdOwner {
   uint32_t mw[G];
-  float2 sg[G];  // sigma (extended: its mantissa), float-float
+  float2 sg[EXT ? G : 1];                  // extended range: sigma's mantissa, float-float
+  unsigned long long sr[EXT ? 1 : G];      // 64-bit mode: sigma (converted at commit)
   int ew[EXT ? G : 1];
   float2 acc[G];   // sum of the successors' r: hits gathered as rows
   float2 accs[G];  // the same for sparse hits (at most two sources), folded in by bwd_fold
@@ -1366,23 +1438,33 @@ template <int G, bool EXT>
 __device__ __forceinline__ void bwd_start(const TK &p, int w, const uint32_t (&mw)[G], BwdOwner<G, EXT> &o) {
   const int lane = lane_id();
   o.bcw = p.nreq == 0 ? p.bc[w] : 0.0;
+  bool mine = false;
 #pragma unroll
   for (int g = 0; g < G; g++) {
     o.mw[g] = mw[g];
-    o.sg[g] = make_float2(1.0f, 0.0f);
     o.acc[g] = make_float2(0.0f, 0.0f);
     o.accs[g] = make_float2(0.0f, 0.0f);
-    if (EXT) o.ew[g] = 0;
+    mine |= (mw[g] >> lane) & 1u;
+  }
+  if constexpr (!EXT) {  // the lane's sigma values in vector loads, used only at commit
+    if (mine) {
+      load_lane<G>(p.sig + sidx<G>(w, 0, lane), o.sr);
+    } else {
+#pragma unroll
+      for (int g = 0; g < (EXT ? 1 : G); g++) o.sr[g] = 1ull;
+    }
+    return;
+  }
+#pragma unroll
+  for (int g = 0; g < (EXT ? G : 1); g++) {
+    o.sg[g] = make_float2(1.0f, 0.0f);
+    o.ew[g] = 0;
     if ((o.mw[g] >> lane) & 1u) {
-      const size_t idx = (size_t)w * (32 * G) + 32 * g + lane;
-      if (EXT) {
-        const bool ov = (p.ovf[(size_t)w * G + g] >> lane) & 1u;
-        const XS x = sig_xs(p, idx, ov);
-        o.sg[g] = ff_mant(x.m);
-        o.ew[g] = x.e;
-      } else {
-        o.sg[g] = ff_u64(p.sig[idx]);
-      }
+      const size_t idx = sidx<G>(w, g, lane);
+      const bool ov = (p.ovf[(size_t)w * G + g] >> lane) & 1u;
+      const XS x = sig_xs(p, idx, ov);
+      o.sg[g] = ff_mant(x.m);
+      o.ew[g] = x.e;
     }
   }
 }
@@ -1401,7 +1483,7 @@ __device__ __forceinline__ void bwd_hit(const TK &p, int v, const uint32_t (&m)[
 #pragma unroll
   for (int g = 0; g < G; g++) {
     if ((m[g] >> lane) & 1u) {
-      const size_t idx = (size_t)v * (32 * G) + 32 * g + lane;
+      const size_t idx = sidx<G>(v, g, lane);
       float2 x = p.r[idx];
       if (EXT) x = ff_scale(x, o.ew[g] - p.xe[idx]);
       ff_add(o.acc[g], x);
@@ -1420,11 +1502,12 @@ __device__ __forceinline__ void bwd_commit(const TK &p, int w, BwdOwner<G, EXT> 
   for (int g = 0; g < G; g++) {
     dl[g] = make_float2(0.0f, 0.0f);
     if ((o.mw[g] >> lane) & 1u) {
-      const size_t idx = (size_t)w * (32 * G) + 32 * g + lane;
+      const size_t idx = sidx<G>(w, g, lane);
+      const float2 sg = EXT ? o.sg[EXT ? g : 0] : ff_u64(o.sr[EXT ? 0 : g]);
       // delta = sigma * sum r(succ);  r = (1 + delta + omega) / sigma = (1 + omega) / sigma + sum
-      dl[g] = ff_mul(p.wsrc[32 * g + lane], ff_mul(o.sg[g], o.acc[g]));
+      dl[g] = ff_mul(p.wsrc[32 * g + lane], ff_mul(sg, o.acc[g]));
       ff_add(contrib, dl[g]);
-      float2 r = ff_mul(om1, ff_rcp(o.sg[g]));
+      float2 r = ff_mul(om1, ff_rcp(sg));
       ff_add(r, o.acc[g]);
       p.r[idx] = r;
       if (EXT) p.xe[idx] = o.ew[g];
@@ -1438,6 +1521,7 @@ __device__ __forceinline__ void bwd_commit(const TK &p, int w, BwdOwner<G, EXT> 
       if (lane == __ffs(act) - 1 && !ff_zero(contrib)) p.bc[w] = o.bcw + ff_to(contrib);
       return;
     }
+    if (!__ballot_sync(BC_FULL, !ff_zero(contrib))) return;  // no successor: delta = 0
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) ff_add(contrib, ff_shfl_xor(contrib, m));
     if (lane == 0 && !ff_zero(contrib)) p.bc[w] = o.bcw + ff_to(contrib);
@@ -1474,11 +1558,11 @@ __device__ __forceinline__ void bwd_hit_load(const TK &p, BwdHit<G, EXT> &h) {
   h.r0 = h.r1 = make_float2(0.0f, 0.0f);
   h.e0 = h.e1 = 0;
   if (!h.sp) return;
-  const size_t i0 = (size_t)h.v * (32 * G) + h.t0;
+  const size_t i0 = sidx<G>(h.v, h.t0);
   h.r0 = p.r[i0];
   if (EXT) h.e0 = p.xe[i0];
   if (h.t1 >= 0) {
-    const size_t i1 = (size_t)h.v * (32 * G) + h.t1;
+    const size_t i1 = sidx<G>(h.v, h.t1);
     h.r1 = p.r[i1];
     if (EXT) h.e1 = p.xe[i1];
   }
@@ -1526,11 +1610,21 @@ __device__ __forceinline__ void bwd_hits_add(const TK &p, const BwdHit<G, EXT> &
       const int jj = hd ? __ffs(hd) - 1 : -1;
       if (hd) hd &= hd - 1;
       const int vq = __shfl_sync(BC_FULL, h.v, jj < 0 ? 0 : jj);
+      bool mine = false;
 #pragma unroll
       for (int g = 0; g < G; g++) {
         const uint32_t m = __shfl_sync(BC_FULL, h.bm[g], jj < 0 ? 0 : jj);
         mq[q][g] = jj < 0 ? 0u : m;
-        xq[q][g] = ((mq[q][g] >> lane) & 1u) ? p.r[(size_t)vq * (32 * G) + 32 * g + lane] : make_float2(0.0f, 0.0f);
+        mine |= (mq[q][g] >> lane) & 1u;
+      }
+      if (mine) {  // the lane's G values of the row in vector loads
+        load_lane<G>(p.r + sidx<G>(vq, 0, lane), xq[q]);
+#pragma unroll
+        for (int g = 0; g < G; g++)
+          if (!((mq[q][g] >> lane) & 1u)) xq[q][g] = make_float2(0.0f, 0.0f);
+      } else {
+#pragma unroll
+        for (int g = 0; g < G; g++) xq[q][g] = make_float2(0.0f, 0.0f);
       }
     }
 #pragma unroll
@@ -1669,7 +1763,7 @@ __device__ __forceinline__ void bwd_lane_pair(const TK &p, int w, int t0, int t1
 #pragma unroll
   for (int z = 0; z < 2; z++) {
     if (ts[z] < 0) continue;
-    const size_t idx = (size_t)w * (32 * G) + ts[z];
+    const size_t idx = sidx<G>(w, ts[z]);
     if (EXT) {
       const bool o = (p.ovf[(size_t)w * G + (ts[z] >> 5)] >> (ts[z] & 31)) & 1u;
       const XS x = sig_xs(p, idx, o);
@@ -1699,7 +1793,7 @@ __device__ __forceinline__ void bwd_lane_pair(const TK &p, int w, int t0, int t1
       for (int z = 0; z < 2; z++) {
         const uint32_t dm = z ? d1[u] : d0[u];
         const bool h = ts[z] >= 0 && ((dm >> (ts[z] & 31)) & 1u);
-        const size_t idx = (size_t)v[u] * (32 * G) + ts[z];
+        const size_t idx = sidx<G>(v[u], ts[z]);
         x[z][u] = h ? p.r[idx] : make_float2(0.0f, 0.0f);
         xe[z][u] = (EXT && h) ? p.xe[idx] : 0;
       }
@@ -1713,7 +1807,7 @@ __device__ __forceinline__ void bwd_lane_pair(const TK &p, int w, int t0, int t1
 #pragma unroll
   for (int z = 0; z < 2; z++) {
     if (ts[z] < 0) continue;
-    const size_t idx = (size_t)w * (32 * G) + ts[z];
+    const size_t idx = sidx<G>(w, ts[z]);
     const float2 dl = ff_mul(p.wsrc[ts[z]], ff_mul(sg[z], acc[z]));
     float2 r = ff_mul(om1, ff_rcp(sg[z]));
     ff_add(r, acc[z]);
@@ -1817,7 +1911,7 @@ __device__ void bwd_lanes(const TK &p, int a0, int a1, const uint32_t *Dn, int g
 // buffers, so one barrier per level suffices.
 template <int G, bool EXT>
 __device__ void phase_bwd_level(const TK &p, int d, int a0, int a1, int Ed, int c0, int c1, int gtid,
-                                int nthr, int gwarp, int nwarps, unsigned char *smem) {
+                                int nthr, int gwarp, int nwarps) {
   const uint32_t *Dn = Fbuf<G>(p, d + 1);
   uint32_t *Dd = Fbuf<G>(p, d);
   uint32_t *Dc = Fbuf<G>(p, d + 2);
@@ -1833,7 +1927,6 @@ __device__ void phase_bwd_level(const TK &p, int d, int a0, int a1, int Ed, int 
   // from a counter, taken by each warp as soon as its walk is done
   const int h0 = p.HEoff[d], h1 = p.HEoff[d + 1];
   int *ctr = &p.ctl->bhubq[d % 3];
-  (void)smem;
   for (;;) {
     int i = 0;
     if (lane_id() == 0) i = atomicAdd(ctr, 1);
@@ -1869,7 +1962,6 @@ __device__ __forceinline__ bool next_dir(const TK &p, bool bu, int ecnt) {
 // ------------------------------------------------------------------ persistent kernel
 template <int G, bool EXT>
 __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fwd_only) {
-  extern __shared__ __align__(16) unsigned char smem[];
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nthr = gridDim.x * blockDim.x;
   const int gwarp = warp_rank(), nwarps = nthr >> 5;
@@ -1892,12 +1984,12 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
       phase_mark<G>(p, level, a_lo, a_hi, ecnt, gwarp, nwarps);
       if (!tsync(p, gs, 1, level)) return;
     }
-    phase_pull<G, EXT>(p, level, bu, a_lo, a_hi, gwarp, nwarps, smem);
+    phase_pull<G, EXT>(p, level, bu, a_lo, a_hi, gwarp, nwarps);
     if (gtid == 0) {
       p.Lbits[level] = 0ull;  // A_level's sources are counted at the next level
       p.ctl->apack[(level + 1) % 3] = 0ull;
       p.ctl->cpack[(level + 1) % 3] = 0ull;
-      p.ctl->chcnt[(level + 1) % 3] = 0;
+      p.ctl->chpk[(level + 1) % 3] = 0ull;
       p.ctl->hubq[(level + 1) % 3] = 0;
       p.ctl->wq[(level + 1) % 3] = 0;
     }
@@ -1937,7 +2029,7 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
       }
       const int a0 = p.Aoff[d], a1 = p.Aoff[d + 1];
       phase_bwd_level<G, EXT>(p, d, a0, a1, level_edges(p, a0, a1), c0, c1, gtid, nthr, gwarp,
-                              nwarps, smem);
+                              nwarps);
       if (gtid == 0) {  // the slots of level d - 1
         p.ctl->bhubq[(d + 2) % 3] = 0;
         p.ctl->bq[(d + 2) % 3] = 0;
@@ -1983,11 +2075,10 @@ __global__ void __launch_bounds__(TPB<G>::value) k_fwd_mark(TK p) {
 
 template <int G, bool EXT>
 __global__ void __launch_bounds__(TPB<G>::value, 1) k_fwd_pull(TK p) {
-  extern __shared__ __align__(16) unsigned char smem[];
   const TileCtl *c = p.ctl;
   if (c->done || c->bar.err) return;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
-  phase_pull<G, EXT>(p, c->level, c->mode != 0, c->a_lo, c->a_hi, warp_rank(), nthr >> 5, smem);
+  const int nthr = gridDim.x * blockDim.x;
+  phase_pull<G, EXT>(p, c->level, c->mode != 0, c->a_lo, c->a_hi, warp_rank(), nthr >> 5);
 }
 
 __global__ void k_fwd_end(TK p) {
@@ -1998,7 +2089,7 @@ __global__ void k_fwd_end(TK p) {
   p.Lbits[level] = 0ull;  // A_level's sources are counted at the next level
   c->apack[(level + 1) % 3] = 0ull;
   c->cpack[(level + 1) % 3] = 0ull;
-  c->chcnt[(level + 1) % 3] = 0;
+  c->chpk[(level + 1) % 3] = 0ull;
   c->hubq[(level + 1) % 3] = 0;
   c->wq[(level + 1) % 3] = 0;
   c->a_pp = c->a_lo;
@@ -2033,7 +2124,6 @@ __global__ void __launch_bounds__(TPB<G>::value) k_bwd_deep(TK p) {
 
 template <int G, bool EXT>
 __global__ void __launch_bounds__(TPB<G>::value, 1) k_bwd_level(TK p) {
-  extern __shared__ __align__(16) unsigned char smem[];
   const TileCtl *c = p.ctl;
   const int d = c->dlevel, lmax = c->lmax;
   if (d < 1 || c->bar.err) return;
@@ -2045,7 +2135,7 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) k_bwd_level(TK p) {
   }
   const int a0 = p.Aoff[d], a1 = p.Aoff[d + 1];
   phase_bwd_level<G, EXT>(p, d, a0, a1, level_edges(p, a0, a1), c0, c1, gtid, nthr, warp_rank(),
-                          nthr >> 5, smem);
+                          nthr >> 5);
 }
 
 __global__ void k_bwd_step(TK p) {
@@ -2080,7 +2170,7 @@ __global__ void k_export(TK p, int lmax, int32_t *depth, unsigned long long *sig
       if ((m >> (t & 31)) & 1u) {
         const size_t o = (size_t)t * p.n + w;
         depth[o] = l;
-        sigma[o] = p.sig[(size_t)w * (32 * G) + t];
+        sigma[o] = p.sig[sidx<G>(w, t)];
         ovf[o] = (p.ovf[(size_t)w * G + (t >> 5)] >> (t & 31)) & 1u;
       }
     }
@@ -2103,6 +2193,14 @@ __global__ void k_lists_fill(int32_t n, const int32_t *rp, const int32_t *flag, 
       RP[pos[v]] = rp[v];
       degs[pos[v]] = rp[v + 1] - rp[v];
     }
+}
+
+// chunk count of each hub: its forward work items
+__global__ void k_hub_chunks(const int32_t *hubs, int nh, const int32_t *rp, int chunk, int32_t *cnt) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nh; k += gridDim.x * blockDim.x) {
+    const int v = hubs[k];
+    cnt[k] = (rp[v + 1] - rp[v] + chunk - 1) / chunk;
+  }
 }
 
 __global__ void k_wsrc(const int32_t *src, int nsrc, const int32_t *omega, float2 *wsrc, int T) {
@@ -2133,44 +2231,37 @@ KPtrs kptrs(int G, bool ext) {
   }
 }
 
-// The dynamic shared-memory size is an attribute of a function on one device: set per
-// device before that device's first launch of the variant.
-std::mutex g_attr_mu;
-bool g_attr_done[128][2][9];
-
-bc_status set_attrs(int G, bool ext) {
-  int dev = 0;
-  BC_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 128) return fail(BC_EINVAL, "tile path: device index out of range");
-  std::lock_guard<std::mutex> lk(g_attr_mu);
-  if (g_attr_done[dev][ext][G]) return BC_OK;
-  const KPtrs k = kptrs(G, ext);
-  for (void *f : {k.persistent, k.pull, k.blevel})
-    BC_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTile));
-  g_attr_done[dev][ext][G] = true;
-  return BC_OK;
-}
-
 }  // namespace
 
 // ================================================================== host side
 static void ws_release(Ctx *ctx, TileWS *ws, bool main, bool ext, bool A) {
   if (main && ws->Hpart) {
     cudaFree(ws->Hpart);
+    cudaFree(ws->FPm);
     ctx->mem.release(nullptr, ws->bytes_hpart);
     ws->Hpart = nullptr;
+    ws->FPm = nullptr;
     ws->hpart_items = 0;
     ws->bytes_hpart = 0;
   }
+  if (main && ws->FPx) {
+    cudaFree(ws->FPx);
+    cudaFree(ws->FPe);
+    ctx->mem.release(nullptr, ws->bytes_hpart_ext);
+    ws->FPx = nullptr;
+    ws->FPe = nullptr;
+    ws->hpart_ext_items = 0;
+    ws->bytes_hpart_ext = 0;
+  }
   if (main && ws->ctl) {
     void *ptrs[] = {ws->vis, ws->F, ws->ovf, ws->cand, ws->sig, ws->r, ws->Aoff, ws->Lbits, ws->HEoff,
-                    ws->C, ws->CPD, ws->CRP, ws->Ch, ws->wsrc, ws->ctl};
+                    ws->C, ws->CPD, ws->CRP, ws->Ch, ws->ChP, ws->Fdone, ws->wsrc, ws->ctl};
     for (void *q : ptrs) cudaFree(q);
     ctx->mem.release(nullptr, ws->bytes_main);
     ws->vis = ws->F = ws->ovf = ws->cand = nullptr;
     ws->sig = nullptr;
     ws->r = nullptr;
-    ws->Aoff = ws->HEoff = ws->C = ws->CPD = ws->CRP = ws->Ch = nullptr;
+    ws->Aoff = ws->HEoff = ws->C = ws->CPD = ws->CRP = ws->Ch = ws->ChP = ws->Fdone = nullptr;
     ws->Lbits = nullptr;
     ws->wsrc = nullptr;
     ws->ctl = nullptr;
@@ -2208,8 +2299,9 @@ static void lists_release(Ctx *ctx, TileWS *ws) {
   cudaFree(ws->Lbu);
   cudaFree(ws->PDbu);
   cudaFree(ws->RPbu);
+  cudaFree(ws->HPbu);
   ctx->mem.release(nullptr, ws->bytes_lists);
-  ws->hubs = ws->Lbu = ws->PDbu = ws->RPbu = nullptr;
+  ws->hubs = ws->Lbu = ws->PDbu = ws->RPbu = ws->HPbu = nullptr;
   ws->lists_for = nullptr;
   ws->bytes_lists = 0;
 }
@@ -2232,7 +2324,7 @@ static bc_status ws_main(Ctx *ctx, TileWS *ws, int n, int T, cudaStream_t st) {
   ws_release(ctx, ws, true, true, true);
   const int G = T / 32;
   const size_t N = (size_t)n, NG = N * G, NT = N * T;
-  const size_t bytes = NG * 4 * 5 + NT * 16 + (N / 32 + 1) * 4 + (N + 3) * 4 + (N + 3) * 8 + N * 16 +
+  const size_t bytes = NG * 4 * 5 + NT * 16 + (N / 32 + 1) * 4 + (N + 3) * 4 + (N + 3) * 8 + N * 24 +
                        T * 8 + sizeof(TileCtl);
   bc_status s = ctx->mem.alloc(nullptr, bytes);
   if (s) return s;
@@ -2250,6 +2342,8 @@ static bc_status ws_main(Ctx *ctx, TileWS *ws, int n, int T, cudaStream_t st) {
   TA(ws->CPD, N * 4);
   TA(ws->CRP, N * 4);
   TA(ws->Ch, N * 4);
+  TA(ws->ChP, N * 4);
+  TA(ws->Fdone, N * 4);
   TA(ws->wsrc, (size_t)T * 8);
   TA(ws->ctl, sizeof(TileCtl));
   ws->n = n;
@@ -2317,36 +2411,73 @@ static bc_status ws_A(Ctx *ctx, TileWS *ws, int64_t cap) {
   return BC_OK;
 }
 
-// Partial sums of the backward work items of one level: a level lists each vertex at most
-// once and splits only entries of degree >= hub_chunk, so it has at most 2 nnz / hub_chunk
-// items.
-static bc_status ws_hpart(Ctx *ctx, TileWS *ws, int64_t nnz, int hub_chunk) {
-  const int64_t items = 2 * nnz / hub_chunk + 16;
-  if (ws->Hpart && ws->hpart_items >= items) return BC_OK;
-  if (ws->Hpart) {
-    cudaFree(ws->Hpart);
-    ctx->mem.release(nullptr, ws->bytes_hpart);
-    ws->Hpart = nullptr;
+// Partial sums of one level's work items (a level lists each vertex at most once).
+static bc_status ws_hpart(Ctx *ctx, TileWS *ws, int64_t nnz, int hub, int hub_chunk, bool ext) {
+  // forward: at most nnz / hub_chunk + nnz / hub items (the chunks, plus one partial chunk
+  // per split candidate); backward: at most 2 nnz / hub_chunk
+  const int64_t items = nnz / hub_chunk + nnz / (hub < hub_chunk ? hub : hub_chunk) + 16;
+  if (!(ws->Hpart && ws->hpart_items >= items)) {
+    if (ws->Hpart) {
+      cudaFree(ws->Hpart);
+      cudaFree(ws->FPm);
+      ctx->mem.release(nullptr, ws->bytes_hpart);
+      ws->Hpart = nullptr;
+      ws->FPm = nullptr;
+      ws->hpart_items = 0;
+    }
+    const size_t bytes = (size_t)items * ws->T * sizeof(float2) + (size_t)items * 2 * ws->G * 4;
+    bc_status s = ctx->mem.alloc(nullptr, bytes);
+    if (s) return s;
+    cudaError_t e = cudaSuccess;
+    TA(ws->Hpart, (size_t)items * ws->T * sizeof(float2));
+    TA(ws->FPm, (size_t)items * 2 * ws->G * 4);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (ws->Hpart) cudaFree(ws->Hpart);
+      if (ws->FPm) cudaFree(ws->FPm);
+      ws->Hpart = nullptr;
+      ws->FPm = nullptr;
+      ctx->mem.release(nullptr, bytes);
+      return fail(BC_ENOMEM, "tile work-item partials allocation failed");
+    }
+    ws->hpart_items = items;
+    ws->bytes_hpart = bytes;
   }
-  const size_t bytes = (size_t)items * ws->T * sizeof(float2);
-  bc_status s = ctx->mem.alloc(nullptr, bytes);
-  if (s) return s;
-  if (cudaMalloc((void **)&ws->Hpart, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    ws->Hpart = nullptr;
-    ctx->mem.release(nullptr, bytes);
-    return fail(BC_ENOMEM, "tile hub-partials allocation failed");
+  if (ext && !(ws->FPx && ws->hpart_ext_items >= items)) {
+    if (ws->FPx) {
+      cudaFree(ws->FPx);
+      cudaFree(ws->FPe);
+      ctx->mem.release(nullptr, ws->bytes_hpart_ext);
+      ws->FPx = nullptr;
+      ws->FPe = nullptr;
+      ws->hpart_ext_items = 0;
+    }
+    const size_t bytes = (size_t)items * ws->T * 12;
+    bc_status s = ctx->mem.alloc(nullptr, bytes);
+    if (s) return s;
+    cudaError_t e = cudaSuccess;
+    TA(ws->FPx, (size_t)items * ws->T * 8);
+    TA(ws->FPe, (size_t)items * ws->T * 4);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (ws->FPx) cudaFree(ws->FPx);
+      if (ws->FPe) cudaFree(ws->FPe);
+      ws->FPx = nullptr;
+      ws->FPe = nullptr;
+      ctx->mem.release(nullptr, bytes);
+      return fail(BC_ENOMEM, "tile extended work-item partials allocation failed");
+    }
+    ws->hpart_ext_items = items;
+    ws->bytes_hpart_ext = bytes;
   }
-  ws->hpart_items = items;
-  ws->bytes_hpart = bytes;
   return BC_OK;
 }
 
-static bc_status ws_lists(Ctx *ctx, TileWS *ws, const DeviceGraph *dg, int hub, cudaStream_t st) {
-  if (ws->hubs && ws->lists_for == dg->rp && ws->lists_hub == hub) return BC_OK;
+static bc_status ws_lists(Ctx *ctx, TileWS *ws, const DeviceGraph *dg, int hub, int chunk, cudaStream_t st) {
+  if (ws->hubs && ws->lists_for == dg->rp && ws->lists_hub == hub && ws->lists_chunk == chunk) return BC_OK;
   lists_release(ctx, ws);
   const size_t N = (size_t)dg->n;
-  const size_t bytes = N * 4 * 4 + 16;
+  const size_t bytes = N * 4 * 5 + 20;
   bc_status s = ctx->mem.alloc(nullptr, bytes);
   if (s) return s;
   cudaError_t e = cudaSuccess;
@@ -2354,6 +2485,7 @@ static bc_status ws_lists(Ctx *ctx, TileWS *ws, const DeviceGraph *dg, int hub, 
   TA(ws->Lbu, N * 4);
   TA(ws->PDbu, N * 4 + 4);
   TA(ws->RPbu, N * 4);
+  TA(ws->HPbu, N * 4 + 4);
   int32_t *flag = nullptr, *pos = nullptr, *degs = nullptr;
   int *d_cnt = nullptr;
   void *scratch = nullptr;
@@ -2382,6 +2514,15 @@ static bc_status ws_lists(Ctx *ctx, TileWS *ws, const DeviceGraph *dg, int hub, 
   if (e == cudaSuccess) e = scan_exclusive_i32(degs, ws->PDbu, (int64_t)h[1] + 1, scratch, st);
   int ebu = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&ebu, ws->PDbu + h[1], 4, cudaMemcpyDeviceToHost, st);
+  // work items of the hubs (bottom-up levels): exclusive prefix of their chunk counts
+  if (e == cudaSuccess) e = cudaMemsetAsync(degs, 0, ((size_t)h[0] + 1) * 4, st);
+  if (e == cudaSuccess && h[0] > 0) {
+    k_hub_chunks<<<ctx->num_sms, 256, 0, st>>>(ws->hubs, h[0], dg->rp, chunk, degs);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = scan_exclusive_i32(degs, ws->HPbu, (int64_t)h[0] + 1, scratch, st);
+  int nitems = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nitems, ws->HPbu + h[0], 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (flag) cudaFree(flag);
   if (pos) cudaFree(pos);
@@ -2396,8 +2537,10 @@ static bc_status ws_lists(Ctx *ctx, TileWS *ws, const DeviceGraph *dg, int hub, 
   ws->nhubs = h[0];
   ws->nbu = h[1];
   ws->Ebu = ebu;
+  ws->nhub_items = nitems;
   ws->lists_for = dg->rp;
   ws->lists_hub = hub;
+  ws->lists_chunk = chunk;
   return BC_OK;
 }
 
@@ -2415,10 +2558,10 @@ static bc_status capture_chunk(cudaStream_t st, cudaGraphExec_t *out, const KPtr
   for (int i = 0; i < kLevelsPerChunk && !s; i++) {
     if (fwd) {
       s = launch(k.mark, grid, block, p, 0, st);
-      if (!s) s = launch(k.pull, grid, block, p, kSmemTile, st);
+      if (!s) s = launch(k.pull, grid, block, p, 0, st);
       if (!s) s = launch((void *)k_fwd_end, dim3(1), dim3(1), p, 0, st);
     } else {
-      s = launch(k.blevel, grid, block, p, kSmemTile, st);
+      s = launch(k.blevel, grid, block, p, 0, st);
       if (!s) s = launch((void *)k_bwd_step, dim3(1), dim3(1), p, 0, st);
     }
   }
@@ -2437,11 +2580,11 @@ static bc_status run_tile(Ctx *ctx, TileWS *ws, TK &p, int G, bool ext, int mode
                           cudaStream_t st, int *derr, int64_t *launches, int *lmax_out) {
   const size_t N = (size_t)ws->n, NG = N * G;
   const KPtrs k = kptrs(G, ext);
-  bc_status s = set_attrs(G, ext);
-  if (s) return s;
+  bc_status s = BC_OK;
   BC_CUDA_TRY(cudaMemsetAsync(ws->F, 0, NG * 4 * 3, st));
   BC_CUDA_TRY(cudaMemsetAsync(ws->ovf, 0, NG * 4, st));
   BC_CUDA_TRY(cudaMemsetAsync(ws->ctl, 0, sizeof(TileCtl), st));
+  BC_CUDA_TRY(cudaMemsetAsync(ws->Fdone, 0, N * 4, st));  // last-finisher counters (a failed tile may leave some set)
   const int nsm = ctx->num_sms;
   const dim3 grid(nsm), block(k.tpb);
   *launches = 0;
@@ -2449,7 +2592,7 @@ static bc_status run_tile(Ctx *ctx, TileWS *ws, TK &p, int G, bool ext, int mode
   if (mode == 0) {
     int fo = fwd_only ? 1 : 0;
     void *args[] = {&p, &fo};
-    const cudaError_t le = cudaLaunchCooperativeKernel(k.persistent, grid, block, args, kSmemTile, st);
+    const cudaError_t le = cudaLaunchCooperativeKernel(k.persistent, grid, block, args, 0, st);
     if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(tile)");
     *launches = 1;
   } else {
@@ -2473,7 +2616,7 @@ static bc_status run_tile(Ctx *ctx, TileWS *ws, TK &p, int G, bool ext, int mode
       } else {
         for (int i = 0; i < kLevelsPerChunk && !s; i++) {
           s = launch(k.mark, grid, block, p, 0, st);
-          if (!s) s = launch(k.pull, grid, block, p, kSmemTile, st);
+          if (!s) s = launch(k.pull, grid, block, p, 0, st);
           if (!s) s = launch((void *)k_fwd_end, dim3(1), dim3(1), p, 0, st);
         }
         if (s) return s;
@@ -2526,7 +2669,7 @@ static bc_status run_tile(Ctx *ctx, TileWS *ws, TK &p, int G, bool ext, int mode
         cudaGraphExecDestroy(gexec);
       } else {
         for (int i = 0; i < nb && !s; i++) {
-          s = launch(k.blevel, grid, block, p, kSmemTile, st);
+          s = launch(k.blevel, grid, block, p, 0, st);
           if (!s) s = launch((void *)k_bwd_step, dim3(1), dim3(1), p, 0, st);
           *launches += 2;
         }
@@ -2559,11 +2702,11 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
   TileWS *ws = *wsp;
   const int hub = a.hub > 0 ? a.hub : kHubDefault;
   const int hub_chunk = a.hub_chunk > 0 ? a.hub_chunk : kHubChunkDefault;
-  if (hub < 64 || hub_chunk < 256 || hub_chunk % 32)
-    return fail(BC_EINVAL, "tile path: hub degree must be >= 64 and hub chunk a multiple of 32, >= 256");
+  if (hub_chunk < 256 || hub_chunk % 32 || hub < 64)
+    return fail(BC_EINVAL, "tile path: hub chunk must be a multiple of 32 and >= 256, hub degree >= 64");
   bc_status s = ws_main(ctx, ws, dg->n, a.T, st);
-  if (!s) s = ws_lists(ctx, ws, dg, hub, st);
-  if (!s) s = ws_hpart(ctx, ws, dg->nnz, hub_chunk);
+  if (!s) s = ws_lists(ctx, ws, dg, hub, hub_chunk, st);
+  if (!s) s = ws_hpart(ctx, ws, dg->nnz, hub, hub_chunk, false);
   if (s) return s;
   const int G = a.T / 32;
   if (!ws->A) {
@@ -2583,6 +2726,7 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
     for (int attempt = 0; attempt < 24; attempt++) {
       if (ext) {
         s = ws_ext(ctx, ws);
+        if (!s) s = ws_hpart(ctx, ws, dg->nnz, hub, hub_chunk, true);
         if (s) break;
       }
       TK p;
@@ -2616,10 +2760,18 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
       p.HEk = ws->HEk;
       p.Hdone = ws->Hdone;
       p.Hpart = ws->Hpart;
+      p.FPs = (unsigned long long *)ws->Hpart;
+      p.FPm = ws->FPm;
+      p.FPx = ws->FPx;
+      p.FPe = ws->FPe;
+      p.Fdone = ws->Fdone;
+      p.HPbu = ws->HPbu;
+      p.nhub_items = ws->nhub_items;
       p.C = ws->C;
       p.CPD = ws->CPD;
       p.CRP = ws->CRP;
       p.Ch = ws->Ch;
+      p.ChP = ws->ChP;
       p.hubs = ws->hubs;
       p.Lbu = ws->Lbu;
       p.PDbu = ws->PDbu;

@@ -234,7 +234,7 @@ extern "C" bc_status bc_autotune(bc_graph *graph, int32_t probe_sources, uint64_
     return cuda_fail(ce, "bc_autotune: copy of the probe sources");
   }
   double best = 1e30, t;
-  Cfg cur{64, 0.2f, 0.f, 0, 2048, 256};
+  Cfg cur{64, 0.2f, 0.f, 0, 512, 256};
   // a later stage's value replaces the current one only when it is clearly faster (2%):
   // timing noise must not pick a threshold
   auto stage = [&](auto set, std::initializer_list<double> vals, double margin) {
@@ -254,9 +254,9 @@ extern "C" bc_status bc_autotune(bc_graph *graph, int32_t probe_sources, uint64_
   stage([](Cfg &c, double v) { c.loop_mode = (int)v; }, {1, 2}, 0.97);
   // stage 4: bottom-up -> top-down hysteresis (0 = none)
   stage([](Cfg &c, double v) { c.beta = (float)v; }, {4, 16}, 0.98);
-  // stage 5: load balance of high-degree vertices (forward: degree pulled by whole CTAs;
-  // backward: edges per warp work item of a split entry)
-  stage([](Cfg &c, double v) { c.hub = (int)v; }, {1024, 4096}, 0.98);
+  // stage 5: load balance of high-degree vertices (forward: degree from which a candidate is
+  // split into warp work items; backward: edges per work item of a split entry)
+  stage([](Cfg &c, double v) { c.hub = (int)v; }, {1024, 2048}, 0.98);
   stage([](Cfg &c, double v) { c.chunk = (int)v; }, {512, 1024}, 0.98);
   // stage 6: the per-source path (the kernel chosen by size, and on larger graphs also one
   // source per CTA, which suits sparse high-diameter graphs); the grid-wide kernel's beta

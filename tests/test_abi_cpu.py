@@ -73,7 +73,10 @@ def test_code_hash_ignores_comments_only(tmp_path):
     a = tmp_path / "a.cu"
     a.write_text(text.replace("// Warp-level work is numbered", "// Warp work is numbered"))
     b = tmp_path / "b.cu"
-    b.write_text(text.replace("constexpr int kHubDefault = 2048;", "constexpr int kHubDefault = 2049;"))
+    import re
+    changed = re.sub(r"constexpr int kHubDefault = (\d+);", r"constexpr int kHubDefault = 1\1;", text)
+    assert changed != text
+    b.write_text(changed)
     assert bench.code_sha1(str(a)) == bench.code_sha1(src) != bench.code_sha1(str(b))
 
 
