@@ -707,6 +707,10 @@ def main():
         side["per_source_path_sample"] = "128 of the 4096 sources"
         side["per_source_roofline_frac"] = (algorithmic_bytes(stp, 1) / stp["seconds"] / 1e9) / peak
         side["tile_sweep_gteps_512_sources"] = sweep
+        # the same step with the sources in the given order (no locality grouping)
+        bc.bc_sources(h, g.n, dsrc, flags | bc.BC_KEEP_ORDER, bc_out=dbc, stream=stream)
+        _, sk = bc.bc_sources(h, g.n, dsrc, flags | bc.BC_KEEP_ORDER, bc_out=dbc, stream=stream)
+        side["given_order_gteps"] = sk["gteps"]
         # R-MAT scale 12, all sources: per-source path vs tiles
         g12 = gg.rmat(12, 16, 1)
         h12 = bc.bc_graph_create(ctx, g12.n, g12.row_ptr, g12.col_idx, g12.nnz, 0)

@@ -88,6 +88,12 @@ enum {
  * bc_autotune cached on the graph (a choice made by timing, so it can differ from one process
  * to the next) is not used; without a path flag the default per-source path runs. */
 #define BC_DETERMINISTIC  (1u << 15)
+/* bc_exact / bc_sources, tile path: run the sources in the given order.  By default a call
+ * of at least four tiles groups its sources by locality first (each source's distances to
+ * 16 seeded landmark vertices, found once per graph, sorted lexicographically): sources
+ * close in the graph share most levels, so a tile's masks are denser and it walks fewer
+ * entries.  The sum over the sources is the same; only its rounding order differs. */
+#define BC_KEEP_ORDER     (1u << 16)
 /* bits 8..11: tile width selector for BC_PATH_TILED: 0 = autotuned, else 32 << (k-1) */
 #define BC_TILE_SHIFT     8
 #define BC_TILE_MASK      (0xFu << BC_TILE_SHIFT)

@@ -19,7 +19,7 @@ __all__ = [
     "bc_stream_submit", "bc_stream_poll", "bc_stream_cancel", "bc_destroy", "bc_sample_sources", "bc_sources_noalloc",
     "bc_set_wait_limit_ms", "BC_OK", "BC_EINVAL", "BC_ENOMEM", "BC_EAGAIN", "BC_ETIMEDOUT",
     "BC_ECUDA", "BC_ENOTFOUND", "BC_ECANCELED", "BC_DEVICE_PTRS", "BC_VALIDATE",
-    "BC_PRUNE_DEG1", "BC_PATH_PLAIN", "BC_PATH_TILED", "BC_LOOP_LAUNCH", "BC_LOOP_GRAPH", "BC_PLAIN_GRID", "BC_DEG2", "BC_PLAIN_CTA", "BC_NO_CD_REUSE", "BC_DETERMINISTIC",
+    "BC_PRUNE_DEG1", "BC_PATH_PLAIN", "BC_PATH_TILED", "BC_LOOP_LAUNCH", "BC_LOOP_GRAPH", "BC_PLAIN_GRID", "BC_DEG2", "BC_PLAIN_CTA", "BC_NO_CD_REUSE", "BC_DETERMINISTIC", "BC_KEEP_ORDER",
     "BC_TILE", "BC_REQ_EXACT_LIST", "BC_REQ_SAMPLED", "LIB_PATH",
 ]
 
@@ -38,6 +38,7 @@ BC_DEG2 = 1 << 12
 BC_PLAIN_CTA = 1 << 13
 BC_NO_CD_REUSE = 1 << 14
 BC_DETERMINISTIC = 1 << 15
+BC_KEEP_ORDER = 1 << 16
 BC_REQ_EXACT_LIST, BC_REQ_SAMPLED = 0, 1
 _STATUS = {0: "BC_OK", 1: "BC_EINVAL", 2: "BC_ENOMEM", 3: "BC_EAGAIN", 4: "BC_ETIMEDOUT",
            5: "BC_ECUDA", 6: "BC_ENOTFOUND", 7: "BC_ECANCELED"}

@@ -206,10 +206,17 @@ bc_status run_sources(Graph *g, const int32_t *d_src, int32_t k, uint32_t flags,
   if (!tiled && !plain) tiled = T > 0;
   if (tiled && !plain) {
     if (!T) T = 64;
+    // sources grouped by locality (at least four tiles; BC_KEEP_ORDER: as given)
+    int32_t *osrc = nullptr;
+    size_t obytes = 0;
+    if (!(flags & BC_KEEP_ORDER) && (int64_t)k >= 4ll * T) {
+      bc_status s = order_sources(g, dg, d_src, k, T, st, &osrc, &obytes);
+      if (s) return s;
+    }
     TileArgs ta{};
     ta.g = dg;
     ta.omega = omega;
-    ta.src = d_src;
+    ta.src = osrc ? osrc : d_src;
     ta.nsrc = k;
     ta.bc = d_bc;
     ta.T = T;
@@ -219,6 +226,10 @@ bc_status run_sources(Graph *g, const int32_t *d_src, int32_t k, uint32_t flags,
     ta.hub = hub;
     ta.hub_chunk = hub_chunk;
     bc_status s = tile_run(ctx, g, &g->tile, ta, st, stats);
+    if (osrc) {
+      cudaStreamSynchronize(st);  // the tile has finished with the ordered list
+      ctx->mem.release(osrc, obytes);
+    }
     if (s) return s;
     (void)leaf_term;
     return BC_OK;
@@ -713,6 +724,7 @@ static void graph_free(Graph *g) {
   c->mem.release(g->g.rp, ((size_t)g->g.n + 1) * 4);
   c->mem.release(g->g.ci, (size_t)g->g.nnz * 4);
   if (g->d_chk) cudaFree(g->d_chk);
+  order_free(c, g);
   g->magic = 0;
   delete g;
 }

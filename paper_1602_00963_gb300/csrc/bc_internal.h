@@ -86,8 +86,9 @@ struct DeviceGraph {
   int32_t *ci = nullptr;
 };
 
-struct TileWS;  // bc_tile.cu
-struct CtaWS;   // bc_cta.cu
+struct TileWS;      // bc_tile.cu
+struct CtaWS;       // bc_cta.cu
+struct OrderCache;  // bc_order.cu
 
 struct PruneCache {
   bool ready = false;
@@ -121,6 +122,7 @@ struct Graph {
   CtaWS *cta = nullptr;    // per-source path on small graphs (bc_cta.cu)
   std::vector<int32_t> h_deg_nonisolated;  // host copy for sampled requests
   int *d_chk = nullptr;    // device words for argument checks (16 bytes, graph's lifetime)
+  OrderCache *order[2] = {nullptr, nullptr};  // landmark distances (graph, residual graph)
 };
 
 struct Server;  // bc_serve.cu
@@ -205,6 +207,14 @@ struct TileArgs {
 bc_status tile_run(Ctx *ctx, Graph *g, TileWS **ws, const TileArgs &a, cudaStream_t st,
                    bc_stats *acc);
 void tile_free(Ctx *ctx, TileWS *ws);
+
+// ---- locality order of the tile path's sources (bc_order.cu)
+// Sources sorted by their distances to seeded landmark vertices (computed once per graph):
+// *out (k ints, device, allocated from the context budget; release *out_bytes) or nullptr
+// when there is nothing to order by.
+bc_status order_sources(Graph *g, const DeviceGraph *dg, const int32_t *d_src, int32_t k, int T,
+                        cudaStream_t st, int32_t **out, size_t *out_bytes);
+void order_free(Ctx *c, Graph *g);
 
 // ---- common helpers (bc_api.cu)
 int64_t plain_bytes(int32_t n);

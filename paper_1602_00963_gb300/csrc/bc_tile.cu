@@ -2157,8 +2157,8 @@ __global__ void k_export(TK p, int lmax, int32_t *depth, unsigned long long *sig
   for (int t = gtid; t < p.nsrc; t += nthr) {  // the sources themselves (also degree 0)
     const size_t o = (size_t)t * p.n + p.src[t];
     depth[o] = 0;
-    sigma[o] = 1ull;
-    ovf[o] = 0;
+    if (sigma) sigma[o] = 1ull;
+    if (ovf) ovf[o] = 0;
   }
   for (int l = 1; l <= lmax; l++) {
     const int a0 = p.Aoff[l], a1 = p.Aoff[l + 1];
@@ -2170,8 +2170,8 @@ __global__ void k_export(TK p, int lmax, int32_t *depth, unsigned long long *sig
       if ((m >> (t & 31)) & 1u) {
         const size_t o = (size_t)t * p.n + w;
         depth[o] = l;
-        sigma[o] = p.sig[sidx<G>(w, t)];
-        ovf[o] = (p.ovf[(size_t)w * G + (t >> 5)] >> (t & 31)) & 1u;
+        if (sigma) sigma[o] = p.sig[sidx<G>(w, t)];
+        if (ovf) ovf[o] = (p.ovf[(size_t)w * G + (t >> 5)] >> (t & 31)) & 1u;
       }
     }
   }
@@ -2860,8 +2860,8 @@ bc_status tile_run(Ctx *ctx, Graph *g, TileWS **wsp, const TileArgs &a, cudaStre
         void *fx = kptrs(G, false).exportk;
         void *args[] = {&p, &lmax, (void *)&a.out_depth, (void *)&a.out_sigma, (void *)&a.out_ovf};
         BC_CUDA_TRY(cudaMemsetAsync(a.out_depth, 0xff, (size_t)nt * ws->n * 4, st));
-        BC_CUDA_TRY(cudaMemsetAsync(a.out_sigma, 0, (size_t)nt * ws->n * 8, st));
-        BC_CUDA_TRY(cudaMemsetAsync(a.out_ovf, 0, (size_t)nt * ws->n, st));
+        if (a.out_sigma) BC_CUDA_TRY(cudaMemsetAsync(a.out_sigma, 0, (size_t)nt * ws->n * 8, st));
+        if (a.out_ovf) BC_CUDA_TRY(cudaMemsetAsync(a.out_ovf, 0, (size_t)nt * ws->n, st));
         BC_CUDA_TRY(cudaLaunchKernel(fx, dim3(ctx->num_sms * 4), dim3(256), args, 0, st));
         BC_CUDA_TRY(cudaStreamSynchronize(st));
       }

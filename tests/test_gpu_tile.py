@@ -249,3 +249,25 @@ def test_repeat_runs(ctx):
         b, _ = bc.bc_exact(h, gc.n, bc.BC_PATH_PLAIN)
         assert np.array_equal(a, b), gc.name
         bc.bc_destroy(h)
+
+
+def test_locality_order_same_sum(ctx):
+    """A call of at least four tiles runs its sources grouped by locality (distances to
+    seeded landmarks); the result is the same sum as in the given order (BC_KEEP_ORDER) and
+    the oracle's, with repeated and isolated sources in the list, on the graph and its
+    residual (pruned) form."""
+    g = gg.rmat(12, 16, 5)
+    h = upload(ctx, g)
+    src = np.concatenate([gg.sample_sources(g, 900, seed=2), [7, 7, 7],
+                          np.flatnonzero(g.degrees() == 0)[:3]]).astype(np.int32)
+    want = oracle.bc(g, src)
+    for T in (32, 64):
+        got, _ = bc.bc_sources(h, g.n, src, TILED | bc.BC_TILE(T))
+        kept, _ = bc.bc_sources(h, g.n, src, TILED | bc.BC_TILE(T) | bc.BC_KEEP_ORDER)
+        assert_bc_close(got, want, what=f"ordered T={T}")
+        assert_bc_close(kept, want, what=f"given order T={T}")
+        again, _ = bc.bc_sources(h, g.n, src, TILED | bc.BC_TILE(T))
+        assert np.array_equal(got, again)
+    pruned, _ = bc.bc_exact(h, g.n, TILED | bc.BC_TILE(32) | bc.BC_PRUNE_DEG1)
+    assert_bc_close(pruned, oracle.bc_exact(g), what="pruned, ordered")
+    bc.bc_destroy(h)
