@@ -233,6 +233,22 @@ extern "C" bc_status bc_autotune(bc_graph *graph, int32_t probe_sources, uint64_
     c->mem.release(pr.d_bc, (size_t)g->g.n * 8);
     return cuda_fail(ce, "bc_autotune: copy of the probe sources");
   }
+  {  // the tile path runs a call's sources grouped by locality: so do the probes
+    int32_t *osrc = nullptr;
+    size_t ob = 0;
+    s = order_sources(g, &g->g, pr.d_src, pr.k, 64, pr.st, &osrc, &ob);
+    if (!s && osrc) {
+      const cudaError_t oe = cudaMemcpyAsync(pr.d_src, osrc, (size_t)pr.k * 4, cudaMemcpyDeviceToDevice, pr.st);
+      cudaStreamSynchronize(pr.st);
+      c->mem.release(osrc, ob);
+      if (oe != cudaSuccess) s = cuda_fail(oe, "bc_autotune: ordered probe sources");
+    }
+    if (s) {
+      c->mem.release(pr.d_src, hs.size() * 4 + 4);
+      c->mem.release(pr.d_bc, (size_t)g->g.n * 8);
+      return s;
+    }
+  }
   double best = 1e30, t;
   Cfg cur{64, 0.2f, 0.f, 0, 512, 256};
   // a later stage's value replaces the current one only when it is clearly faster (2%):
