@@ -90,7 +90,7 @@ enum {
 #define BC_DETERMINISTIC  (1u << 15)
 /* bc_exact / bc_sources, tile path: run the sources in the given order.  By default a call
  * of at least four tiles groups its sources by locality first (each source's distances to
- * 16 seeded landmark vertices, found once per graph, sorted lexicographically): sources
+ * 32 seeded landmark vertices, found once per graph, sorted lexicographically): sources
  * close in the graph share most levels, so a tile's masks are denser and it walks fewer
  * entries.  The sum over the sources is the same; only its rounding order differs. */
 #define BC_KEEP_ORDER     (1u << 16)

@@ -25,7 +25,7 @@ namespace bcl {
 
 std::vector<int64_t> sample_distinct(int64_t N, int64_t k, uint64_t seed);  // bc_tune.cu
 
-constexpr int kLandmarks = 16;
+constexpr int kLandmarks = 32;
 constexpr uint64_t kLandmarkSeed = 0x1A4D3A12C0FFEEull;
 
 struct OrderCache {
