@@ -460,14 +460,39 @@ __device__ __forceinline__ void walk(const TK &p, const int32_t *L, const int32_
 template <int G, bool EXT>
 struct PullAcc {
   unsigned long long s[G];
-  uint32_t o;  // per-lane overflow bits, bit g
+  uint32_t o;   // per-lane overflow bits, bit g
+  uint32_t cy;  // 64-bit mode: carries out of this lane's additions (any group)
   uint32_t newm[G];
   XS x[EXT ? G : 1];
 };
 
+// s += v with the carry out of bit 63 counted in cy (one carry-chained pair of adds).
+__device__ __forceinline__ void add_carry(unsigned long long &s, uint32_t &cy, unsigned long long v) {
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+l"(s), "+r"(cy) : "l"(v));
+}
+
+// Sparse forward terms in 64-bit mode on tiles of up to 128 sources: per warp, one 64-bit
+// accumulator per source in shared memory.  A sparse hit's lane adds its (source, sigma)
+// pairs with shared atomics (integer sums, so their order does not matter) and the owner's
+// lanes fold the accumulators in before committing, leaving them zero.
+template <int G>
+__device__ __forceinline__ unsigned long long *sparse_acc() {
+  __shared__ unsigned long long s_acc[G <= 4 ? 32 * 32 * G : 1];
+  return s_acc + (size_t)(threadIdx.x >> 5) * (32 * G);
+}
+template <int G>
+__device__ __forceinline__ void sparse_acc_clear() {
+  if constexpr (G <= 4) {
+    unsigned long long *a = sparse_acc<G>() - (size_t)(threadIdx.x >> 5) * (32 * G);
+    for (int i = threadIdx.x; i < 32 * 32 * G; i += blockDim.x) a[i] = 0ull;
+    __syncthreads();
+  }
+}
+
 template <int G, bool EXT>
 __device__ __forceinline__ void pull_init(PullAcc<G, EXT> &a) {
   a.o = 0u;
+  a.cy = 0u;
 #pragma unroll
   for (int g = 0; g < G; g++) {
     a.s[g] = 0ull;
@@ -525,7 +550,7 @@ __device__ __forceinline__ bool pull_commit(const TK &p, int w, int level, const
     if (!m) continue;
     any = true;
     const bool mine = (m >> lane) & 1u;
-    const bool og = (a.o >> g) & 1u;
+    const bool og = ((a.o >> g) & 1u) || (!EXT && a.cy != 0u);
     const size_t idx = sidx<G>(w, g, lane);
     if (mine) {
       p.sig[idx] = a.s[g];
@@ -693,10 +718,36 @@ __device__ __forceinline__ void fwd_hits_add(const TK &p, const FwdHit<G, EXT> &
     }
     return;
   }
-  while (hs) {
-    const int jj = __ffs(hs) - 1;
-    hs &= hs - 1;
-    fwd_sparse_take<G, EXT>(h, jj, a);
+  if constexpr (G <= 4) {  // each sparse lane adds its pairs to the warp's accumulators
+    if (hs) {
+      unsigned long long *sa = sparse_acc<G>();
+      bool carry = false;
+      uint32_t nb[G];
+#pragma unroll
+      for (int g = 0; g < G; g++) nb[g] = 0u;
+      if ((hs >> lane) & 1u) {
+        unsigned long long old = atomicAdd(&sa[h.t0], h.s0);
+        carry = old + h.s0 < old;
+        if (h.t1 >= 0) {
+          old = atomicAdd(&sa[h.t1], h.s1);
+          carry = carry || old + h.s1 < old;
+        }
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+          if ((h.t0 >> 5) == g) nb[g] |= 1u << (h.t0 & 31);
+          if (h.t1 >= 0 && (h.t1 >> 5) == g) nb[g] |= 1u << (h.t1 & 31);
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < G; g++) a.newm[g] |= __reduce_or_sync(BC_FULL, nb[g]);
+      if (__ballot_sync(BC_FULL, carry)) a.cy |= 1u;
+    }
+  } else {
+    while (hs) {
+      const int jj = __ffs(hs) - 1;
+      hs &= hs - 1;
+      fwd_sparse_take<G, EXT>(h, jj, a);
+    }
   }
   // 64-bit mode (EXT is handled above): an overflowed parent has already flagged the tile
   // for the extended rerun, so only the additions' carries are checked
@@ -730,11 +781,29 @@ __device__ __forceinline__ void fwd_hits_add(const TK &p, const FwdHit<G, EXT> &
 #pragma unroll
       for (int g = 0; g < G; g++) {
         a.newm[g] |= mq[q][g];
-        const unsigned long long old = a.s[g];
-        a.s[g] = old + sv[q][g];
-        if (a.s[g] < old) a.o |= 1u << g;
+        add_carry(a.s[g], a.cy, sv[q][g]);
       }
     }
+  }
+}
+
+// 64-bit mode, tiles of up to 128 sources: fold the warp's shared sparse accumulators of the
+// current owner into a and clear them (before every commit of a pulled vertex).
+template <int G, bool EXT>
+__device__ __forceinline__ void sparse_fold(PullAcc<G, EXT> &a) {
+  if constexpr (!EXT && G <= 4) {
+    unsigned long long *sa = sparse_acc<G>();
+    const int lane = lane_id();
+    __syncwarp();
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      const unsigned long long v = sa[32 * g + lane];
+      if (v) {
+        add_carry(a.s[g], a.cy, v);
+        sa[32 * g + lane] = 0ull;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -791,6 +860,7 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
       const int jl = __ffs(hs | hd) - 1;
       const int wk = __shfl_sync(BC_FULL, w, jl);
       if (wk != cur) {
+        sparse_fold<G, EXT>(a);
         if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
           abuf_push(p, ab, cur, ap, a_base);
         cur = wk;
@@ -801,6 +871,7 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
       fwd_hits_add<G, EXT>(p, h, hs, hd, a);
     }
   });
+  sparse_fold<G, EXT>(a);
   if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
     abuf_push(p, ab, cur, ap, a_base);
 }
@@ -846,13 +917,14 @@ __device__ void fwd_warp_item(const TK &p, int level, const int32_t *L, const in
     fwd_hit_load<G, EXT>(p, h);
     fwd_hits_add<G, EXT>(p, h, __ballot_sync(BC_FULL, h.sp), __ballot_sync(BC_FULL, h.hit && !h.sp), a);
   }
+  sparse_fold<G, EXT>(a);
   if (nch > 1) {
     unsigned long long *ps = p.FPs + (size_t)i * (32 * G);
     uint32_t *pm = p.FPm + (size_t)i * (2 * G);
 #pragma unroll
     for (int g = 0; g < G; g++) {
       __stcg(&ps[32 * g + lane], a.s[g]);
-      const unsigned ob = __ballot_sync(BC_FULL, (a.o >> g) & 1u);
+      const unsigned ob = __ballot_sync(BC_FULL, ((a.o >> g) & 1u) || (!EXT && a.cy != 0u));
       if (lane == 0) {
         __stcg(&pm[g], a.newm[g]);
         __stcg(&pm[G + g], ob);
@@ -1966,6 +2038,7 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
   const int nthr = gridDim.x * blockDim.x;
   const int gwarp = warp_rank(), nwarps = nthr >> 5;
   GridSync *gs = &p.ctl->bar;
+  sparse_acc_clear<G>();
   phase_init_vis<G>(p, gtid, nthr);
   if (!tsync(p, gs, 0, 0)) return;
   if (gtid == 0) init_sources<G>(p);
@@ -2077,6 +2150,7 @@ template <int G, bool EXT>
 __global__ void __launch_bounds__(TPB<G>::value, 1) k_fwd_pull(TK p) {
   const TileCtl *c = p.ctl;
   if (c->done || c->bar.err) return;
+  sparse_acc_clear<G>();
   const int nthr = gridDim.x * blockDim.x;
   phase_pull<G, EXT>(p, c->level, c->mode != 0, c->a_lo, c->a_hi, warp_rank(), nthr >> 5);
 }
