@@ -133,4 +133,52 @@ __device__ __forceinline__ float2 ff_shfl_xor(float2 a, int m) {
   return make_float2(__shfl_xor_sync(BC_FULL, a.x, m), __shfl_xor_sync(BC_FULL, a.y, m));
 }
 
+// ------------------------------------------------------------------ paired float-float
+// Two float-float values (of two sources) in packed registers: hi = {hi_a, hi_b}, lo =
+// {lo_a, lo_b}.  The packed f32x2 additions of sm_100 and later round each half as the scalar
+// __fadd_rn / __fsub_rn do (round to nearest even, subnormals kept), so ff2_add computes on
+// each half exactly the sequence of ff_add: results are bit for bit those of two ff_add calls,
+// in half the instructions.
+struct FF2 {
+  unsigned long long hi, lo;
+};
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long r, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ FF2 ff2_pack(float2 a, float2 b) {
+  FF2 r;
+  r.hi = f2_pack(a.x, b.x);
+  r.lo = f2_pack(a.y, b.y);
+  return r;
+}
+__device__ __forceinline__ void ff2_unpack(FF2 r, float2 &a, float2 &b) {
+  f2_unpack(r.hi, a.x, b.x);
+  f2_unpack(r.lo, a.y, b.y);
+}
+// ff_add on both halves (Knuth's two-sum of the high parts, then the renormalisation)
+__device__ __forceinline__ void ff2_add(FF2 &a, FF2 b) {
+  const unsigned long long s = f2_add(a.hi, b.hi);
+  const unsigned long long bb = f2_sub(s, a.hi);
+  const unsigned long long e = f2_add(f2_sub(a.hi, f2_sub(s, bb)), f2_sub(b.hi, bb));
+  const unsigned long long t = f2_add(e, f2_add(a.lo, b.lo));
+  const unsigned long long hi = f2_add(s, t);
+  a.lo = f2_sub(t, f2_sub(hi, s));
+  a.hi = hi;
+}
+
 }  // namespace bcl

@@ -1674,6 +1674,47 @@ __device__ __forceinline__ void bwd_hits_add(const TK &p, const BwdHit<G, EXT> &
     return;
   }
   // up to HB<G>::value successors at a time: their r-row loads are in flight together
+  if constexpr (G % 2 == 0) {  // the lane's sources in pairs, summed by packed additions
+    if (!hd) return;
+    FF2 acc2[G / 2];
+#pragma unroll
+    for (int j = 0; j < G / 2; j++) acc2[j] = ff2_pack(o.acc[2 * j], o.acc[2 * j + 1]);
+    while (hd) {
+      FF2 xq[HB<G>::value][G / 2];
+      uint32_t mq[HB<G>::value][G];
+#pragma unroll
+      for (int q = 0; q < HB<G>::value; q++) {
+        const int jj = hd ? __ffs(hd) - 1 : -1;
+        if (hd) hd &= hd - 1;
+        const int vq = __shfl_sync(BC_FULL, h.v, jj < 0 ? 0 : jj);
+        bool mine = false;
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+          const uint32_t m = __shfl_sync(BC_FULL, h.bm[g], jj < 0 ? 0 : jj);
+          mq[q][g] = jj < 0 ? 0u : m;
+          mine |= (mq[q][g] >> lane) & 1u;
+        }
+        const float4 *row = (const float4 *)(p.r + sidx<G>(vq, 0, lane));
+#pragma unroll
+        for (int j = 0; j < G / 2; j++) {
+          float4 x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          if (mine) x = row[j];  // (hi, lo) of source 2j, then of 2j + 1
+          if (!((mq[q][2 * j] >> lane) & 1u)) x.x = x.y = 0.0f;
+          if (!((mq[q][2 * j + 1] >> lane) & 1u)) x.z = x.w = 0.0f;
+          xq[q][j].hi = f2_pack(x.x, x.z);
+          xq[q][j].lo = f2_pack(x.y, x.w);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < HB<G>::value; q++)
+#pragma unroll
+        for (int j = 0; j < G / 2; j++)
+          if (mq[q][2 * j] | mq[q][2 * j + 1]) ff2_add(acc2[j], xq[q][j]);
+    }
+#pragma unroll
+    for (int j = 0; j < G / 2; j++) ff2_unpack(acc2[j], o.acc[2 * j], o.acc[2 * j + 1]);
+    return;
+  }
   while (hd) {
     float2 xq[HB<G>::value][G];
     uint32_t mq[HB<G>::value][G];
