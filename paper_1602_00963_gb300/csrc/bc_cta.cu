@@ -25,6 +25,7 @@
 #include <climits>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "bc_ff.cuh"
 #include "bc_internal.h"
@@ -57,6 +58,10 @@ struct CtaK {
   int32_t *out_depth;         // forward-only export of src[0] (sssp), or null
   unsigned long long *out_sigma;
   uint8_t *out_ovf;
+  // several requests in one launch (nreq > 0): request q owns the sources
+  // [req[q], req[q + 1]) and the CTAs [req[R + q], req[R + q + 1]), R = nreq + 1
+  int nreq;
+  const int32_t *req;
 };
 
 // State of one source, n vertices: sigma u64 | r float2 | depth i32 | queue i32 | overflow
@@ -556,7 +561,16 @@ __global__ void __launch_bounds__(kCtaThreads, 2) k_cta_sources(CtaK p) {
     if ((unsigned long long)lmax > my_deep) my_deep = (unsigned long long)lmax;
     if (sh.ovf) my_ovf++;
   };
-  for (int si = blockIdx.x; si < p.nsrc; si += gridDim.x) {
+  int s0 = (int)blockIdx.x, s1 = p.nsrc, sstep = (int)gridDim.x;
+  if (p.nreq > 0) {  // the sources of this CTA's request, strided over the request's CTAs
+    const int32_t *rc = p.req + p.nreq + 1;
+    int q = 0;
+    while (q + 1 < p.nreq && (int)blockIdx.x >= rc[q + 1]) q++;
+    s0 = p.req[q] + ((int)blockIdx.x - rc[q]);
+    s1 = p.req[q + 1];
+    sstep = rc[q + 1] - rc[q];
+  }
+  for (int si = s0; si < s1; si += sstep) {
     const int s = p.src[si];
     int qtot = 0;
     const int lmax = cta_forward(p, A, s, sh, &qtot, &my_arcs);
@@ -610,6 +624,18 @@ __global__ void k_cta_reduce(const double *bcp, int ncta, int n, double *bc) {
   }
 }
 
+// Several requests: req_bc[q][v] += sum over request q's CTAs c (in order) of bcp[c][v]
+// (rc: the requests' CTA ranges, nreq + 1 offsets).
+__global__ void k_cta_reduce_req(const double *bcp, int nreq, const int32_t *rc, double *const *req_bc, int n) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    for (int q = 0; q < nreq; q++) {
+      double sum = 0.0;
+      for (int c = rc[q]; c < rc[q + 1]; c++) sum += bcp[(size_t)c * n + v];
+      if (sum != 0.0) req_bc[q][v] += sum;
+    }
+  }
+}
+
 }  // namespace
 
 struct CtaWS {
@@ -619,6 +645,7 @@ struct CtaWS {
   double *bcp = nullptr;
   char *gws = nullptr;
   unsigned long long *stats = nullptr;
+  int32_t *req = nullptr;  // request offsets of a launch with several requests
   size_t bytes = 0;
 };
 
@@ -627,6 +654,7 @@ void cta_free(Ctx *ctx, CtaWS *ws) {
   cudaFree(ws->bcp);
   cudaFree(ws->gws);
   cudaFree(ws->stats);
+  cudaFree(ws->req);
   ctx->mem.release(nullptr, ws->bytes);
   delete ws;
 }
@@ -680,7 +708,7 @@ static bc_status cta_ensure(Ctx *ctx, CtaWS **wsp, int n, bool tri) {
   ws->slice = slice;
   ws->tri = tri ? 1 : 0;
   const size_t b_bcp = (size_t)ncta * n * 8, b_gws = ws->slice * ncta;
-  ws->bytes = b_bcp + b_gws + 64;
+  ws->bytes = b_bcp + b_gws + 64 + 2 * (kCtaMaxReq + 1) * sizeof(int32_t);
   bc_status s = ctx->mem.alloc(nullptr, ws->bytes);
   if (s) {
     delete ws;
@@ -689,6 +717,7 @@ static bc_status cta_ensure(Ctx *ctx, CtaWS **wsp, int n, bool tri) {
   cudaError_t e = cudaMalloc((void **)&ws->bcp, b_bcp);
   if (e == cudaSuccess) e = cudaMalloc((void **)&ws->gws, b_gws);
   if (e == cudaSuccess) e = cudaMalloc((void **)&ws->stats, 64);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&ws->req, 2 * (kCtaMaxReq + 1) * sizeof(int32_t));
   if (e != cudaSuccess) {
     cudaGetLastError();
     cta_free(ctx, ws);
@@ -729,19 +758,95 @@ bc_status cta_run(Ctx *ctx, Graph *g, CtaWS **wsp, const PlainArgs &a, cudaStrea
   p.out_ovf = a.out_ovf;
   p.tri = a.tri;
   p.ntri = sssp ? 0 : a.ntri;
-  const int ncta = std::max(1, std::min(ws->ncta, std::max(p.nsrc, p.ntri)));
+  if (a.nreq > 0 && (sssp || p.ntri || a.nreq > kCtaMaxReq || !a.h_req_k || !a.req_bc))
+    return fail(BC_EINVAL, "CTA per-source kernel: bad request list");
+  // requests per launch: groups of consecutive requests, each request with CTAs of its own
+  // (at most ws->ncta requests per launch)
+  std::vector<std::vector<int32_t>> hreq;
+  int nlaunch = 0, launched_max = 0;
   BC_CUDA_TRY(cudaMemsetAsync(ws->stats, 0, 64, st));
   cudaEvent_t e0, e1;
   BC_CUDA_TRY(cudaEventCreate(&e0));
   BC_CUDA_TRY(cudaEventCreate(&e1));
   cudaEventRecord(e0, st);
   const bool was_clean = ws->clean;
-  ws->clean = false;  // until the launch is known to have completed
-  k_cta_sources<<<ncta, kCtaThreads, ws->smem, st>>>(p);
-  cudaError_t le = cudaGetLastError();
-  if (le == cudaSuccess && !sssp && a.bc) {
-    k_cta_reduce<<<ctx->num_sms * 4, 256, 0, st>>>(ws->bcp, ncta, n, a.bc);
+  ws->clean = false;  // until the launches are known to have completed
+  cudaError_t le = cudaSuccess;
+  auto launch = [&](const CtaK &kp, int ncta, const int32_t *rc, double *const *rbc) {
+    CtaK q = kp;
+    q.clean = (was_clean || launched_max >= ncta) ? 1 : 0;
+    k_cta_sources<<<ncta, kCtaThreads, ws->smem, st>>>(q);
     le = cudaGetLastError();
+    launched_max = std::max(launched_max, ncta);
+    nlaunch++;
+    if (le == cudaSuccess && !sssp && q.nreq > 0) {
+      k_cta_reduce_req<<<ctx->num_sms * 4, 256, 0, st>>>(ws->bcp, q.nreq, rc, rbc, n);
+      le = cudaGetLastError();
+    } else if (le == cudaSuccess && !sssp && a.bc) {
+      k_cta_reduce<<<ctx->num_sms * 4, 256, 0, st>>>(ws->bcp, ncta, n, a.bc);
+      le = cudaGetLastError();
+    }
+  };
+  if (a.nreq <= 0) {
+    launch(p, std::max(1, std::min(ws->ncta, std::max(p.nsrc, p.ntri))), nullptr, nullptr);
+  } else {
+    int q0 = 0, soff = 0;
+    while (q0 < a.nreq && le == cudaSuccess) {
+      const int q1 = std::min(a.nreq, q0 + ws->ncta);
+      const int R = q1 - q0;
+      long long K = 0;
+      for (int q = q0; q < q1; q++) K += a.h_req_k[q];
+      const int C = (int)std::max<long long>(R, std::min<long long>(ws->ncta, K));
+      // CTAs in proportion to the sources (at least one each, at most one per source), then
+      // the rest, one at a time, to the request with the most rounds of sources per CTA
+      std::vector<int> c(R);
+      int used = 0;
+      for (int j = 0; j < R; j++) {
+        const long long k = a.h_req_k[q0 + j];
+        c[j] = (int)std::max<long long>(1, std::min<long long>(k, K > 0 ? C * k / K : 1));
+        used += c[j];
+      }
+      while (used > C) {
+        int jm = -1;
+        for (int j = 0; j < R; j++)
+          if (c[j] > 1 && (jm < 0 || c[j] > c[jm])) jm = j;
+        if (jm < 0) break;
+        c[jm]--;
+        used--;
+      }
+      while (used < C) {
+        int jm = -1;
+        long long best = 0;
+        for (int j = 0; j < R; j++) {
+          const long long k = a.h_req_k[q0 + j];
+          const long long rounds = (k + c[j] - 1) / c[j];
+          if (c[j] < k && rounds > best) {
+            best = rounds;
+            jm = j;
+          }
+        }
+        if (jm < 0) break;
+        c[jm]++;
+        used++;
+      }
+      std::vector<int32_t> &h = hreq.emplace_back(2 * (R + 1));
+      h[0] = 0;
+      h[R + 1] = 0;
+      for (int j = 0; j < R; j++) {
+        h[j + 1] = h[j] + a.h_req_k[q0 + j];
+        h[R + 2 + j] = h[R + 1 + j] + c[j];
+      }
+      le = cudaMemcpyAsync(ws->req, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+      if (le != cudaSuccess) break;
+      CtaK kp = p;
+      kp.src = a.src + soff;
+      kp.nsrc = h[R];
+      kp.nreq = R;
+      kp.req = ws->req;
+      launch(kp, used, ws->req + R + 1, a.req_bc + q0);
+      soff += h[R];
+      q0 = q1;
+    }
   }
   cudaEventRecord(e1, st);
   if (le != cudaSuccess) {
@@ -759,7 +864,7 @@ bc_status cta_run(Ctx *ctx, Graph *g, CtaWS **wsp, const PlainArgs &a, cudaStrea
   if (se != cudaSuccess) return cuda_fail(se, "CTA per-source kernel");
   BC_CUDA_TRY(cudaStreamSynchronize(st));
   // the launched CTAs left their state cleared; CTAs not launched kept theirs
-  ws->clean = was_clean || ncta == ws->ncta;
+  ws->clean = was_clean || launched_max == ws->ncta;
   if (acc) {
     acc->seconds += ms * 1e-3;
     acc->sources += p.nsrc + 3ll * p.ntri;
@@ -768,7 +873,7 @@ bc_status cta_run(Ctx *ctx, Graph *g, CtaWS **wsp, const PlainArgs &a, cudaStrea
     acc->reached_arcs += (int64_t)hs[1];
     acc->levels += (int64_t)hs[2];
     if ((int32_t)hs[3] > acc->max_depth) acc->max_depth = (int32_t)hs[3];
-    acc->kernel_launches += sssp ? 1 : 2;
+    acc->kernel_launches += sssp ? nlaunch : 2 * nlaunch;
     if (acc->tile_width == 0) acc->tile_width = 1;
   }
   return BC_OK;

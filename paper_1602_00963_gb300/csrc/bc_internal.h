@@ -161,6 +161,12 @@ struct PlainArgs {
   // grid-wide kernel only: rescan each level's degree prefix in the backward sweep
   // instead of reusing the forward's (ablation of Sec. 3.1's reuse)
   bool no_cd_reuse;
+  // per-CTA kernel (serving): the sources of nreq requests in one call, request q's being
+  // the next h_req_k[q] entries of src (host array); each request gets its own CTAs and
+  // its BC goes to req_bc[q] (device array of nreq device pointers); bc is then unused
+  int32_t nreq;
+  const int32_t *h_req_k;
+  double *const *req_bc;
 };
 bc_status plain_ensure(Ctx *ctx, PlainWS *ws, int32_t n);
 void plain_free(Ctx *ctx, PlainWS *ws);
@@ -171,6 +177,7 @@ bc_status plain_run_view(const PlainWS &ws, const PlainArgs &a, int num_sms, uin
 // ---- per-source path on small graphs: one CTA per source (bc_cta.cu)
 constexpr int32_t kCtaMaxN = 65536;        // default for the per-source path up to this size
 constexpr int32_t kCtaForcedMaxN = 1 << 24;  // BC_PLAIN_CTA / tuned: up to this size
+constexpr int kCtaMaxReq = 32;  // requests per per-CTA launch (serving)
 bool cta_fits(int32_t n);
 // Runs a.src, one source per CTA (a.out_depth set: forward only for a.src[0], depth / sigma /
 // overflow exported).

@@ -12,8 +12,9 @@
 //   * run the tile with per-phase launches (not the cooperative kernel) so that tiles of
 //     different graphs, on different streams, overlap on the device;
 //   * on small graphs (up to 65,536 vertices), and on graphs the autotuner gave to it,
-//     instead run one request's remaining sources on the per-source CTA kernel (each CTA a
-//     source at a time, all SMs busy), which there is far faster than a tile;
+//     instead run the remaining sources of all the graph's admitted requests (up to
+//     kCtaMaxReq) in one call of the per-source CTA kernel, each request on CTAs of its
+//     own (each CTA a source at a time), which there is far faster than a tile;
 //   * complete a request when its last tile is done: copy its BC to the caller's buffer.
 // A request that arrives while others run is admitted as soon as memory allows and its
 // sources join the next tiles of its graph.
@@ -39,6 +40,8 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int kWorkers = 4;
 constexpr int kMaxReqPerTile = 8;
+// request-buffer pointers per graph: a tile's requests or a per-CTA launch's
+constexpr int kReqPtrs = kCtaMaxReq > kMaxReqPerTile ? kCtaMaxReq : kMaxReqPerTile;
 
 struct Req {
   uint64_t id = 0;
@@ -103,7 +106,7 @@ void exec_release(Ctx *c, GraphExec *e) {
   if (e->d_many) c->mem.release(e->d_many, e->cap_many * 4);
   if (e->d_src) c->mem.release(e->d_src, 256 * 4);
   if (e->d_lane) c->mem.release(e->d_lane, 256);
-  if (e->d_reqbc) c->mem.release(e->d_reqbc, kMaxReqPerTile * sizeof(double *));
+  if (e->d_reqbc) c->mem.release(e->d_reqbc, kReqPtrs * sizeof(double *));
 }
 
 void finish(Server *sv, Req *r, bc_status st) {
@@ -168,7 +171,7 @@ bc_status exec_buffers(Ctx *c, GraphExec *e) {
   if (e->d_src) return BC_OK;
   bc_status s = c->mem.alloc((void **)&e->d_src, 256 * 4);
   if (!s) s = c->mem.alloc((void **)&e->d_lane, 256);
-  if (!s) s = c->mem.alloc((void **)&e->d_reqbc, kMaxReqPerTile * sizeof(double *));
+  if (!s) s = c->mem.alloc((void **)&e->d_reqbc, kReqPtrs * sizeof(double *));
   return s;
 }
 
@@ -181,6 +184,7 @@ void worker_main(Server *sv, int wid) {
   std::vector<uint8_t> hlane;
   std::vector<double *> hreq;
   std::vector<std::pair<Req *, int>> slots;
+  std::vector<int32_t> hk;
   std::unique_lock<std::mutex> lk(sv->mu);
   while (!sv->stop) {
     admit(sv);
@@ -202,27 +206,35 @@ void worker_main(Server *sv, int wid) {
     if (cta_fits(g->g.n) || (g->tune.ready && g->tune.res.tile_width == 0 && g->tune.res.plain_cta &&
                              g->g.n <= kCtaForcedMaxN)) {
       // small graph (or one the autotuner gave to the per-CTA kernel): the remaining sources
-      // of its first unscheduled request, one launch
-      Req *r = nullptr;
-      for (Req *q : sv->active)
-        if (q->g == g && !q->canceled && q->next < q->src.size()) {
-          r = q;
-          break;
+      // of up to kCtaMaxReq of its admitted requests, in admission order, in one call; each
+      // request gets CTAs of its own, so requests that arrived while the last call ran share
+      // the next one instead of waiting for one call each
+      hsrc.clear();
+      hreq.clear();
+      hk.clear();
+      slots.clear();
+      for (Req *q : sv->active) {
+        if ((int)slots.size() >= kCtaMaxReq) break;
+        if (q->g != g || q->canceled || q->next >= q->src.size()) continue;
+        const int take = (int)(q->src.size() - q->next);
+        hsrc.insert(hsrc.end(), q->src.begin() + (long)q->next, q->src.end());
+        q->next = q->src.size();
+        q->inflight++;
+        if (!q->started) {
+          q->started = true;
+          q->t_start = Clock::now();
+          q->queue_s = std::chrono::duration<double>(q->t_start - q->t_submit).count();
         }
-      const size_t k = r->src.size() - r->next;
-      hsrc.assign(r->src.begin() + (long)r->next, r->src.end());
-      r->next = r->src.size();
-      r->inflight++;
-      if (!r->started) {
-        r->started = true;
-        r->t_start = Clock::now();
-        r->queue_s = std::chrono::duration<double>(r->t_start - r->t_submit).count();
+        hk.push_back(take);
+        hreq.push_back(q->d_bc);
+        slots.emplace_back(q, take);
       }
+      const size_t k = hsrc.size();
       job->busy = true;
       job->counted = true;
       lk.unlock();
-      bc_status s = BC_OK;
-      if (job->cap_many < k) {
+      bc_status s = exec_buffers(c, job);
+      if (!s && job->cap_many < k) {
         if (job->d_many) c->mem.release(job->d_many, job->cap_many * 4);
         job->d_many = nullptr;
         job->cap_many = 0;
@@ -231,20 +243,28 @@ void worker_main(Server *sv, int wid) {
       }
       if (!s && cudaMemcpyAsync(job->d_many, hsrc.data(), k * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
         s = fail(BC_ECUDA, "serving: copy of request sources");
+      if (!s && cudaMemcpyAsync(job->d_reqbc, hreq.data(), hreq.size() * sizeof(double *), cudaMemcpyHostToDevice,
+                                st) != cudaSuccess)
+        s = fail(BC_ECUDA, "serving: copy of request buffers");
       if (!s) {
         PlainArgs pa{};
         pa.g = &g->g;
         pa.src = job->d_many;
         pa.nsrc = (int32_t)k;
-        pa.bc = r->d_bc;
         pa.max_degree = g->max_degree;
+        pa.nreq = (int32_t)slots.size();
+        pa.h_req_k = hk.data();
+        pa.req_bc = job->d_reqbc;
         s = cta_run(c, g, &job->cta, pa, st, nullptr);
       }
       lk.lock();
       job->busy = false;
-      r->inflight--;
-      if (s && r->status == BC_OK) r->status = s;
-      if (r->inflight == 0) finish(sv, r, r->status);
+      for (auto &sl : slots) {
+        Req *q = sl.first;
+        q->inflight--;
+        if (s && q->status == BC_OK) q->status = s;
+        if (q->inflight == 0) finish(sv, q, q->status);
+      }
       sv->cv_work.notify_all();
       continue;
     }

@@ -116,6 +116,30 @@ def test_budget_admission_completes_all():
         bc.bc_destroy(c)
 
 
+def test_per_cta_requests_share_calls_under_a_tight_budget():
+    """Requests on a small graph (per-CTA kernel) submitted together share calls, each
+    request on CTAs of its own; with an HBM budget that leaves fewer CTAs than requests,
+    the requests are split over several launches.  Every result matches the oracle."""
+    g = gg.rmat(11, 8, 52)
+    c = bc.bc_ctx_create(0, 1200 << 10)
+    try:
+        h = upload(c, g)
+        rng = np.random.Generator(np.random.PCG64(7))
+        pool = np.flatnonzero(g.degrees() > 0)
+        ids = []
+        for i in range(10):
+            out = np.zeros(g.n)
+            src = rng.choice(pool, size=int(rng.integers(1, 12)), replace=False).astype(np.int32)
+            ids.append((bc.bc_stream_submit(c, h, out, bc.BC_REQ_EXACT_LIST, src=src), src, out))
+        for rid, src, out in ids:
+            st, res = bc.bc_stream_poll(c, rid, -1)
+            assert st == bc.BC_OK and res["status"] == bc.BC_OK, res
+            assert_bc_close(out, oracle.bc(g, src), what="per-CTA request under a tight budget")
+        bc.bc_destroy(h)
+    finally:
+        bc.bc_destroy(c)
+
+
 def test_autotune_and_tuned_dispatch(ctx):
     g = gg.rmat(12, 16, 1)
     h = upload(ctx, g)
