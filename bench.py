@@ -340,7 +340,7 @@ def serving_bench(bc, ctx, per_rate=300, lam0=8.0, lam_max=1024.0, seed=100):
     pool = serving_pool()
     handles = [bc.bc_graph_create(ctx, g.n, g.row_ptr, g.col_idx, g.nnz, 0) for _, g in pool]
     for (_, g), h in zip(pool, handles):  # kernel choice per graph (not timed)
-        if g.n > 65536:
+        if g.n > 4096:
             bc.bc_autotune(h, 64, 7)
     nonisolated = [np.flatnonzero(g.degrees() > 0).astype(np.int32) for _, g in pool]
     for gi, (_, g) in enumerate(pool):  # workspaces set up before the sweep

@@ -11,7 +11,7 @@
 //     dependencies are routed to its own request's accumulator);
 //   * run the tile with per-phase launches (not the cooperative kernel) so that tiles of
 //     different graphs, on different streams, overlap on the device;
-//   * on small graphs (up to 65,536 vertices), and on graphs the autotuner gave to it,
+//   * on graphs the autotuner gave to the per-source path (untuned: up to 65,536 vertices),
 //     instead run the remaining sources of all the graph's admitted requests (up to
 //     kCtaMaxReq) in one call of the per-source CTA kernel, each request on CTAs of its
 //     own (each CTA a source at a time), which there is far faster than a tile;
@@ -88,6 +88,16 @@ struct Server {
 
 namespace {
 
+// Kernel of a graph's requests: the autotuner's choice when the graph was tuned (the per-CTA
+// kernel when it picked the per-source path, tiles otherwise), else by size (per-CTA up to
+// 65,536 vertices).
+bool serve_on_cta(const Graph *g) {
+  if (g->tune.ready)
+    return g->tune.res.tile_width == 0 && (g->tune.res.plain_cta || cta_fits(g->g.n)) &&
+           g->g.n <= kCtaForcedMaxN;
+  return cta_fits(g->g.n);
+}
+
 int tile_width_for(Graph *g) {
   if (g->tune.ready && g->tune.res.tile_width > 0) return g->tune.res.tile_width;
   return 64;
@@ -95,8 +105,7 @@ int tile_width_for(Graph *g) {
 
 size_t tile_ws_estimate(Graph *g, int T) {
   const size_t n = (size_t)g->g.n, G = (size_t)T / 32;
-  if (cta_fits(g->g.n) || (g->tune.ready && g->tune.res.tile_width == 0 && g->tune.res.plain_cta))
-    return n * 64;  // CTA kernel: it shrinks its partials to the budget
+  if (serve_on_cta(g)) return n * 64;  // CTA kernel: it shrinks its partials to the budget
   return n * G * 20 + n * T * 16 + n * (20 + 12 * G) * 4;
 }
 
@@ -203,8 +212,7 @@ void worker_main(Server *sv, int wid) {
       continue;
     }
     Graph *g = job->g;
-    if (cta_fits(g->g.n) || (g->tune.ready && g->tune.res.tile_width == 0 && g->tune.res.plain_cta &&
-                             g->g.n <= kCtaForcedMaxN)) {
+    if (serve_on_cta(g)) {
       // small graph (or one the autotuner gave to the per-CTA kernel): the remaining sources
       // of up to kCtaMaxReq of its admitted requests, in admission order, in one call; each
       // request gets CTAs of its own, so requests that arrived while the last call ran share

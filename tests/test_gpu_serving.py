@@ -149,4 +149,16 @@ def test_autotune_and_tuned_dispatch(ctx):
     got, st = bc.bc_exact(h, g.n)  # no path flag: uses the tuned configuration
     assert st["tile_width"] == (t["tile_width"] or 1)
     assert_bc_close(got, oracle.bc_exact(g, nthreads=8), what="tuned exact")
+    # serving follows the tuned kernel too (tiles or the per-CTA kernel, whichever won)
+    rng = np.random.Generator(np.random.PCG64(3))
+    ids = []
+    for i in range(6):
+        out = np.zeros(g.n)
+        src = rng.choice(np.flatnonzero(g.degrees() > 0), size=int(rng.integers(1, 100)), replace=False)
+        src = src.astype(np.int32)
+        ids.append((bc.bc_stream_submit(ctx, h, out, bc.BC_REQ_EXACT_LIST, src=src), src, out))
+    for rid, src, out in ids:
+        st, res = bc.bc_stream_poll(ctx, rid, -1)
+        assert st == bc.BC_OK and res["status"] == bc.BC_OK, res
+        assert_bc_close(out, oracle.bc(g, src), what="request on a tuned graph")
     bc.bc_destroy(h)
