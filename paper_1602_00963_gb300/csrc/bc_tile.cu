@@ -255,6 +255,21 @@ __device__ __forceinline__ void load_lane(const float2 *a, float2 (&out)[G]) {
   }
 }
 
+// Ask L2 for the 128-byte lines of a [32][G] row of 8-byte values (lane-major) that hold the
+// sources of mask m.  Dense hits gather their rows a few at a time, later in the step; lines
+// requested here are then on their way while the rows before them are summed.
+template <int G>
+__device__ __forceinline__ void prefetch_row(const void *row, const uint32_t (&m)[G]) {
+  constexpr int L = 16 / G;  // lanes per line
+  uint32_t u = 0u;
+#pragma unroll
+  for (int g = 0; g < G; g++) u |= m[g];
+#pragma unroll
+  for (int k = 0; k < 2 * G; k++)
+    if ((u >> (k * L)) & ((1u << L) - 1u))
+      asm volatile("prefetch.global.L2 [%0];" ::"l"((const char *)row + 128 * k));
+}
+
 // Row v of a [n][G] mask array in one or two vector loads (rows are 4G-byte aligned).
 template <int G>
 __device__ __forceinline__ void load_row(const uint32_t *a, long long v, uint32_t (&out)[G]) {
@@ -1778,6 +1793,7 @@ __device__ void bwd_walk(const TK &p, int a0, int a1, int E, const uint32_t *Dn,
       }
     }
     bwd_hit_load<G, EXT>(p, h);
+    if (h.hit && !h.sp) prefetch_row<G>(p.r + sidx<G>(h.v, 0, 0), h.bm);
     const unsigned vm = __ballot_sync(BC_FULL, valid);
     const unsigned sps = __ballot_sync(BC_FULL, h.sp);
     const unsigned dns = __ballot_sync(BC_FULL, h.hit && !h.sp);
@@ -1818,24 +1834,42 @@ __device__ void bwd_warp_item(const TK &p, int i, int h0, const uint32_t *Dn) {
   BwdOwner<G, EXT> o;
   bwd_start_k<G, EXT>(p, k, o);
   const int e0 = p.rp[w] + c * p.hub_chunk, e1 = min(p.rp[w + 1], e0 + p.hub_chunk);
-  for (int base = e0; base < e1; base += 32) {
-    const int jdx = base + lane;
-    BwdHit<G, EXT> h;
-    h.v = jdx < e1 ? p.ci[jdx] : -1;
-    h.hit = false;
-    if (h.v >= 0) {
-      load_row<G>(Dn, h.v, h.bm);
-    } else {
+  // a pipeline over the 32-edge steps: neighbour ids two steps ahead, their masks one step
+  // ahead (in flight while a step's hits are summed), and the dense rows of the next step
+  // requested from L2 as soon as its masks are in
+  int vn = e0 + lane < e1 ? p.ci[e0 + lane] : -1;
+  uint32_t bn[G];
 #pragma unroll
-      for (int g = 0; g < G; g++) h.bm[g] = 0u;
-    }
+  for (int g = 0; g < G; g++) bn[g] = 0u;
+  if (vn >= 0) load_row<G>(Dn, vn, bn);
+  int vnn = e0 + 32 + lane < e1 ? p.ci[e0 + 32 + lane] : -1;
+  for (int base = e0; base < e1; base += 32) {
+    BwdHit<G, EXT> h;
+    h.v = vn;
+    h.hit = false;
 #pragma unroll
     for (int g = 0; g < G; g++) {
-      h.bm[g] &= o.mw[g];
+      h.bm[g] = bn[g] & o.mw[g];
       h.hit |= h.bm[g] != 0u;
     }
+    vn = vnn;
+#pragma unroll
+    for (int g = 0; g < G; g++) bn[g] = 0u;
+    if (vn >= 0) load_row<G>(Dn, vn, bn);
+    vnn = base + 64 + lane < e1 ? p.ci[base + 64 + lane] : -1;
     bwd_hit_load<G, EXT>(p, h);
+    if (h.hit && !h.sp) prefetch_row<G>(p.r + sidx<G>(h.v, 0, 0), h.bm);
     bwd_hits_add<G, EXT>(p, h, __ballot_sync(BC_FULL, h.sp), __ballot_sync(BC_FULL, h.hit && !h.sp), o);
+    if (vn >= 0) {  // the next step's dense rows
+      uint32_t m[G];
+      int nb = 0;
+#pragma unroll
+      for (int g = 0; g < G; g++) {
+        m[g] = bn[g] & o.mw[g];
+        nb += __popc(m[g]);
+      }
+      if (nb > kSparse) prefetch_row<G>(p.r + sidx<G>(vn, 0, 0), m);
+    }
   }
   if (nch == 1) {
     bwd_commit<G, EXT>(p, w, o);
