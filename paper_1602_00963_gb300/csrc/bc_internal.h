@@ -222,6 +222,11 @@ void tile_free(Ctx *ctx, TileWS *ws);
 bc_status order_sources(Graph *g, const DeviceGraph *dg, const int32_t *d_src, int32_t k, int T,
                         cudaStream_t st, int32_t **out, size_t *out_bytes);
 void order_free(Ctx *c, Graph *g);
+// Host copy of the same profiles, [n][*L] bytes (source v's L distances at v * L), built on
+// first use with tile workspace *ws (the caller holds g->mu); *keys = nullptr, *L = 0 when
+// there is nothing to order by.  Valid until the graph is destroyed.
+bc_status order_host_keys(Graph *g, const DeviceGraph *dg, int T, cudaStream_t st, TileWS **ws,
+                          const uint8_t **keys, int *L);
 
 // ---- common helpers (bc_api.cu)
 int64_t plain_bytes(int32_t n);

@@ -33,6 +33,7 @@ struct OrderCache {
   int L = 0;                    // landmarks (0: nothing to order by)
   uint8_t *d = nullptr;         // [L][n] distances, 255 = unreached or >= 255
   size_t bytes = 0;
+  std::vector<uint8_t> h;       // host copy, [n][L] (serving), filled on first use
 };
 
 namespace {
@@ -53,7 +54,7 @@ __global__ void k_lm_gather(const uint8_t *d, int L, int n, const int32_t *src, 
   }
 }
 
-bc_status build_cache(Graph *g, const DeviceGraph *dg, int T, cudaStream_t st, OrderCache *oc) {
+bc_status build_cache(Graph *g, const DeviceGraph *dg, int T, cudaStream_t st, TileWS **ws, OrderCache *oc) {
   Ctx *c = g->ctx;
   const int32_t n = dg->n;
   std::vector<int32_t> rp((size_t)n + 1);
@@ -85,7 +86,7 @@ bc_status build_cache(Graph *g, const DeviceGraph *dg, int T, cudaStream_t st, O
     ta.loop_mode = 0;
     ta.alpha = 0.5f;
     ta.out_depth = d_depth;
-    s = tile_run(c, g, &g->tile, ta, st, nullptr);
+    s = tile_run(c, g, ws, ta, st, nullptr);
   }
   if (!s) {
     k_lm_pack<<<c->num_sms * 4, 256, 0, st>>>(d_depth, (size_t)L * n, oc->d);
@@ -120,25 +121,67 @@ void order_free(Ctx *c, Graph *g) {
   }
 }
 
-bc_status order_sources(Graph *g, const DeviceGraph *dg, const int32_t *d_src, int32_t k, int T, cudaStream_t st,
-                        int32_t **out, size_t *out_bytes) {
+namespace {
+
+// The graph's cache (built on first use)
+bc_status cache_for(Graph *g, const DeviceGraph *dg, int T, cudaStream_t st, TileWS **ws, OrderCache **out) {
   Ctx *c = g->ctx;
-  *out = nullptr;
-  *out_bytes = 0;
   OrderCache *oc = nullptr;
   for (OrderCache *x : g->order)
     if (x && x->rp == dg->rp) oc = x;
   if (!oc) {
-    OrderCache *&slot = g->order[g->order[0] && g->order[0]->rp != dg->rp ? 1 : 0];
-    if (slot) {  // a cache for another graph of this handle (the residual one): replace it
+    // an empty slot, else the one not holding the handle's own graph (whose host copy serving
+    // keeps using): a cache for an earlier residual graph is replaced
+    int si = !g->order[0] ? 0 : !g->order[1] ? 1 : (g->order[0]->rp == g->g.rp ? 1 : 0);
+    OrderCache *&slot = g->order[si];
+    if (slot) {
       if (slot->d) c->mem.release(slot->d, slot->bytes);
       delete slot;
     }
     slot = new (std::nothrow) OrderCache();
     if (!slot) return fail(BC_ENOMEM, "source order: host allocation failed");
     oc = slot;
-    bc_status s = build_cache(g, dg, T, st, oc);
+    bc_status s = build_cache(g, dg, T, st, ws, oc);
     if (s) return s;
+  }
+  *out = oc;
+  return BC_OK;
+}
+
+}  // namespace
+
+bc_status order_host_keys(Graph *g, const DeviceGraph *dg, int T, cudaStream_t st, TileWS **ws,
+                          const uint8_t **keys, int *L) {
+  *keys = nullptr;
+  *L = 0;
+  OrderCache *oc = nullptr;
+  bc_status s = cache_for(g, dg, T, st, ws, &oc);
+  if (s || oc->L == 0) return s;
+  const size_t n = (size_t)dg->n, Lc = (size_t)oc->L;
+  if (oc->h.empty()) {
+    std::vector<uint8_t> t(Lc * n);
+    cudaError_t e = cudaMemcpyAsync(t.data(), oc->d, t.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "source order: copy of the landmark distances");
+    std::vector<uint8_t> h(Lc * n);
+    for (size_t l = 0; l < Lc; l++)
+      for (size_t v = 0; v < n; v++) h[v * Lc + l] = t[l * n + v];
+    oc->h.swap(h);
+  }
+  *keys = oc->h.data();
+  *L = oc->L;
+  return BC_OK;
+}
+
+bc_status order_sources(Graph *g, const DeviceGraph *dg, const int32_t *d_src, int32_t k, int T, cudaStream_t st,
+                        int32_t **out, size_t *out_bytes) {
+  Ctx *c = g->ctx;
+  *out = nullptr;
+  *out_bytes = 0;
+  OrderCache *oc = nullptr;
+  {
+    const bc_status s0 = cache_for(g, dg, T, st, &g->tile, &oc);
+    if (s0) return s0;
   }
   if (oc->L == 0) return BC_OK;
   const int L = oc->L;

@@ -69,7 +69,14 @@ struct GraphExec {
   double **d_reqbc = nullptr;
   bool busy = false;
   bool counted = false;
+  bool keys_tried = false;      // tiles: landmark profiles looked up (host copy)
+  const uint8_t *keys = nullptr;  // [n][nkeys] distances to the landmarks, or null
+  int nkeys = 0;
 };
+
+// Tiles are cut from the pending sources of a graph's oldest requests, up to this many
+// tiles' worth, grouped by their landmark profiles.
+constexpr int kOrderWindow = 16;
 
 }  // namespace
 
@@ -184,6 +191,82 @@ bc_status exec_buffers(Ctx *c, GraphExec *e) {
   return s;
 }
 
+struct Cand {
+  const uint8_t *key;  // the source's landmark profile
+  int ri, pos;         // request (index in the window) and position in its source list
+};
+
+void mark_started(Req *r) {
+  if (!r->started) {
+    r->started = true;
+    r->t_start = Clock::now();
+    r->queue_s = std::chrono::duration<double>(r->t_start - r->t_submit).count();
+  }
+}
+
+// One tile of graph g from the pending sources of its oldest requests (at most kOrderWindow
+// tiles' worth), sorted by landmark profile: the T sources nearest in that order to the
+// oldest request's next source (so that request always advances), from at most
+// kMaxReqPerTile requests.  Each request's taken sources move to the front of its pending
+// part; lanes are grouped by request.
+void select_by_locality(Server *sv, Graph *g, const uint8_t *keys, int L, int T, std::vector<Cand> &cand,
+                        std::vector<std::pair<int, int>> &chosen, std::vector<int32_t> &hsrc,
+                        std::vector<uint8_t> &hlane, std::vector<double *> &hreq,
+                        std::vector<std::pair<Req *, int>> &slots) {
+  std::vector<Req *> rq;
+  cand.clear();
+  chosen.clear();
+  for (Req *r : sv->active) {
+    if (r->g != g || r->canceled || r->next >= r->src.size()) continue;
+    if (!rq.empty() && cand.size() >= (size_t)kOrderWindow * T) break;
+    const int ri = (int)rq.size();
+    rq.push_back(r);
+    for (size_t i = r->next; i < r->src.size(); i++)
+      cand.push_back(Cand{keys + (size_t)r->src[i] * L, ri, (int)i});
+  }
+  if (rq.empty()) return;
+  std::sort(cand.begin(), cand.end(), [L](const Cand &a, const Cand &b) {
+    const int c = memcmp(a.key, b.key, (size_t)L);
+    if (c != 0) return c < 0;
+    return a.ri != b.ri ? a.ri < b.ri : a.pos < b.pos;
+  });
+  int a = 0;
+  while (!(cand[a].ri == 0 && cand[a].pos == (int)rq[0]->next)) a++;
+  std::vector<int> used;  // requests in the tile
+  auto take = [&](int i) {
+    const int ri = cand[i].ri;
+    if (std::find(used.begin(), used.end(), ri) == used.end()) {
+      if ((int)used.size() >= kMaxReqPerTile) return;
+      used.push_back(ri);
+    }
+    chosen.emplace_back(ri, cand[i].pos);
+  };
+  take(a);
+  for (int l = a - 1, h = a + 1; (int)chosen.size() < T && (l >= 0 || h < (int)cand.size());) {
+    if (h < (int)cand.size()) take(h++);
+    if ((int)chosen.size() < T && l >= 0) take(l--);
+  }
+  std::sort(chosen.begin(), chosen.end());
+  for (size_t i = 0; i < chosen.size();) {
+    const int ri = chosen[i].first;
+    Req *r = rq[(size_t)ri];
+    const uint8_t slot = (uint8_t)slots.size();
+    const size_t first = r->next;
+    for (; i < chosen.size() && chosen[i].first == ri; i++) {
+      std::swap(r->src[r->next], r->src[(size_t)chosen[i].second]);
+      r->next++;
+    }
+    for (size_t j = first; j < r->next; j++) {
+      hsrc.push_back(r->src[j]);
+      hlane.push_back(slot);
+    }
+    r->inflight++;
+    mark_started(r);
+    hreq.push_back(r->d_bc);
+    slots.emplace_back(r, (int)(r->next - first));
+  }
+}
+
 void worker_main(Server *sv, int wid) {
   Ctx *c = sv->ctx;
   cudaSetDevice(c->device);
@@ -194,6 +277,8 @@ void worker_main(Server *sv, int wid) {
   std::vector<double *> hreq;
   std::vector<std::pair<Req *, int>> slots;
   std::vector<int32_t> hk;
+  std::vector<Cand> cand;
+  std::vector<std::pair<int, int>> chosen;
   std::unique_lock<std::mutex> lk(sv->mu);
   while (!sv->stop) {
     admit(sv);
@@ -277,11 +362,30 @@ void worker_main(Server *sv, int wid) {
       continue;
     }
     const int T = tile_width_for(g);
+    if (!job->keys_tried) {  // the graph's landmark profiles (once; the graph stays ours)
+      job->busy = true;
+      lk.unlock();
+      const uint8_t *keys = nullptr;
+      int nkeys = 0;
+      {
+        std::lock_guard<std::mutex> glk(g->mu);
+        if (order_host_keys(g, &g->g, T, st, &job->ws, &keys, &nkeys) != BC_OK) {
+          keys = nullptr;  // tiles in admission order instead
+          nkeys = 0;
+        }
+      }
+      lk.lock();
+      job->keys = keys;
+      job->nkeys = nkeys;
+      job->keys_tried = true;
+    }
     hsrc.clear();
     hlane.clear();
     hreq.clear();
     slots.clear();
-    for (Req *r : sv->active) {
+    if (job->keys) {
+      select_by_locality(sv, g, job->keys, job->nkeys, T, cand, chosen, hsrc, hlane, hreq, slots);
+    } else for (Req *r : sv->active) {
       if ((int)hsrc.size() >= T || (int)slots.size() >= kMaxReqPerTile) break;
       if (r->g != g || r->canceled || r->next >= r->src.size()) continue;
       const int take = (int)std::min<size_t>((size_t)(T - (int)hsrc.size()), r->src.size() - r->next);

@@ -56,6 +56,32 @@ def test_mixed_requests_equal_alone(ctx):
         bc.bc_destroy(h)
 
 
+def test_tile_requests_grouped_by_locality(ctx):
+    """A graph above 65,536 vertices is served with tiles; requests submitted together are
+    cut into tiles by landmark profile across requests (at most 8 requests per tile, the
+    oldest request always advancing).  Each result equals the request run alone and, for
+    the first (12 sources), the oracle."""
+    g = gg.rmat(17, 4, 41)
+    h = upload(ctx, g)
+    rng = np.random.Generator(np.random.PCG64(17))
+    pool = np.flatnonzero(g.degrees() > 0)
+    reqs = []
+    for i in range(12):
+        out = np.zeros(g.n)
+        k = 12 if i == 0 else int(rng.integers(1, 160))
+        src = rng.choice(pool, size=k, replace=False).astype(np.int32)
+        reqs.append((bc.bc_stream_submit(ctx, h, out, bc.BC_REQ_EXACT_LIST, src=src), src, out))
+    for i, (rid, src, out) in enumerate(reqs):
+        st, res = bc.bc_stream_poll(ctx, rid, -1)
+        assert st == bc.BC_OK and res["status"] == bc.BC_OK, res
+        assert res["sources"] == len(src)
+        alone, _ = bc.bc_sources(h, g.n, src)
+        assert_bc_close(out, alone, what=f"request {rid} grouped vs alone")
+        if i == 0:
+            assert_bc_close(out, oracle.bc(g, src), what="grouped request vs oracle")
+    bc.bc_destroy(h)
+
+
 def test_sampled_is_deterministic_and_scaled(ctx):
     g = gg.rmat(10, 8, 31)
     h = upload(ctx, g)
