@@ -226,7 +226,7 @@ def code_sha1(path: str) -> str:
 def ncu_traffic(T: int, tiles_bytes: float):
     """DRAM bytes (read + write) per launch of the tile kernel from the committed ncu
     summary, if it was taken on the current kernel code and this tile width."""
-    path = os.path.join(ROOT, "profiles", "tile_rmat20_dram.json")
+    path = os.path.join(ROOT, "profiles", f"tile_rmat20_dram_T{T}.json")
     src = os.path.join(ROOT, "paper_1602_00963_gb300", "csrc", "bc_tile.cu")
     try:
         with open(path) as f:
