@@ -1500,11 +1500,18 @@ __device__ void phase_bwd_deep(const TK &p, int a0, int a1, int gtid, int nthr) 
   }
 }
 
+// Tiles of 128 sources or more (64-bit mode) load the owner's sigma and BC at its commit
+// instead of holding them in registers through the walk (registers bind there).
+template <int G, bool EXT>
+struct LateOwner {
+  static constexpr bool value = !EXT && G >= 4;
+};
+
 template <int G, bool EXT>
 struct BwdOwner {
   uint32_t mw[G];
   float2 sg[EXT ? G : 1];                  // extended range: sigma's mantissa, float-float
-  unsigned long long sr[EXT ? 1 : G];      // 64-bit mode: sigma (converted at commit)
+  unsigned long long sr[(EXT || LateOwner<G, EXT>::value) ? 1 : G];  // 64-bit mode: sigma
   int ew[EXT ? G : 1];
   float2 acc[G];   // sum of the successors' r: hits gathered as rows
   float2 accs[G];  // the same for sparse hits (at most two sources), folded in by bwd_fold
@@ -1526,7 +1533,7 @@ __device__ __forceinline__ void bwd_fold(BwdOwner<G, EXT> &o) {
 template <int G, bool EXT>
 __device__ __forceinline__ void bwd_start(const TK &p, int w, const uint32_t (&mw)[G], BwdOwner<G, EXT> &o) {
   const int lane = lane_id();
-  o.bcw = p.nreq == 0 ? p.bc[w] : 0.0;
+  if constexpr (!LateOwner<G, EXT>::value) o.bcw = p.nreq == 0 ? p.bc[w] : 0.0;
   bool mine = false;
 #pragma unroll
   for (int g = 0; g < G; g++) {
@@ -1535,7 +1542,9 @@ __device__ __forceinline__ void bwd_start(const TK &p, int w, const uint32_t (&m
     o.accs[g] = make_float2(0.0f, 0.0f);
     mine |= (mw[g] >> lane) & 1u;
   }
-  if constexpr (!EXT) {  // the lane's sigma values in vector loads, used only at commit
+  if constexpr (LateOwner<G, EXT>::value) {
+    return;
+  } else if constexpr (!EXT) {  // the lane's sigma values in vector loads, used only at commit
     if (mine) {
       load_lane<G>(p.sig + sidx<G>(w, 0, lane), o.sr);
     } else {
@@ -1587,12 +1596,31 @@ __device__ __forceinline__ void bwd_commit(const TK &p, int w, BwdOwner<G, EXT> 
   const float2 om1 = ff_u64(1ull + (p.omega ? (unsigned long long)p.omega[w] : 0ull));
   float2 contrib = make_float2(0.0f, 0.0f);
   float2 dl[G];
+  unsigned long long sl[LateOwner<G, EXT>::value ? G : 1];
+  if constexpr (LateOwner<G, EXT>::value) {
+    o.bcw = p.nreq == 0 ? p.bc[w] : 0.0;
+    bool mine = false;
+#pragma unroll
+    for (int g = 0; g < G; g++) mine |= (o.mw[g] >> lane) & 1u;
+    if (mine) {
+      load_lane<G>(p.sig + sidx<G>(w, 0, lane), sl);
+    } else {
+#pragma unroll
+      for (int g = 0; g < G; g++) sl[g] = 1ull;
+    }
+  }
 #pragma unroll
   for (int g = 0; g < G; g++) {
     dl[g] = make_float2(0.0f, 0.0f);
     if ((o.mw[g] >> lane) & 1u) {
       const size_t idx = sidx<G>(w, g, lane);
-      const float2 sg = EXT ? o.sg[EXT ? g : 0] : ff_u64(o.sr[EXT ? 0 : g]);
+      float2 sg;
+      if constexpr (EXT)
+        sg = o.sg[g];
+      else if constexpr (LateOwner<G, EXT>::value)
+        sg = ff_u64(sl[g]);
+      else
+        sg = ff_u64(o.sr[g]);
       // delta = sigma * sum r(succ);  r = (1 + delta + omega) / sigma = (1 + omega) / sigma + sum
       dl[g] = ff_mul(p.wsrc[32 * g + lane], ff_mul(sg, o.acc[g]));
       ff_add(contrib, dl[g]);
