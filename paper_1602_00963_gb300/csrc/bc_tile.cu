@@ -878,17 +878,19 @@ __device__ void pull_walk(const TK &p, int level, const int32_t *L, const int32_
       const int wk = __shfl_sync(BC_FULL, w, jl);
       if (wk != cur) {
         sparse_fold<G, EXT>(a);
+        if (G >= 8 && cur >= 0) load_row<G>(p.vis, cur, visc);  // reloaded (registers bind at T = 256)
         if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
           abuf_push(p, ab, cur, ap, a_base);
         cur = wk;
 #pragma unroll
-        for (int g = 0; g < G; g++) visc[g] = __shfl_sync(BC_FULL, vw[g], jl);
+        for (int g = 0; g < G; g++) visc[g] = G >= 8 ? 0u : __shfl_sync(BC_FULL, vw[g], jl);
         pull_init(a);
       }
       fwd_hits_add<G, EXT>(p, h, hs, hd, a);
     }
   });
   sparse_fold<G, EXT>(a);
+  if (G >= 8 && cur >= 0) load_row<G>(p.vis, cur, visc);
   if (cur >= 0 && pull_commit<G, EXT>(p, cur, level, a, visc, leaf, nsacc))
     abuf_push(p, ab, cur, ap, a_base);
 }
