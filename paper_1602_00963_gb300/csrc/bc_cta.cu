@@ -689,10 +689,11 @@ static bc_status cta_ensure(Ctx *ctx, CtaWS **wsp, int n, bool tri) {
   const size_t slice = ((in_smem ? 0 : st) + cta_extra_bytes(n) +
                         (tri ? st + cta_extra_bytes(n) + (size_t)n * 8 : 0) + 255) & ~(size_t)255;
   const size_t per_cta = (size_t)n * 8 + slice;
-  if (ctx->mem.budget) {  // fewer CTAs when the context's HBM budget is tight
+  if (ctx->mem.budget) {  // fewer CTAs when the context's HBM budget is tight: at most half
+    // of what is free, so that requests arriving meanwhile still find room (serving)
     const size_t used = ctx->mem.used.load() - (ws ? ws->bytes : 0);
     const size_t avail = ctx->mem.budget > used + 64 ? ctx->mem.budget - used - 64 : 0;
-    ncta = (int)std::min<size_t>((size_t)ncta, avail / per_cta);
+    ncta = (int)std::min<size_t>((size_t)ncta, std::max<size_t>(avail / 2 / per_cta, avail >= per_cta ? 1 : 0));
     if (ncta < 1) return fail(BC_ENOMEM, "CTA per-source workspace exceeds the context HBM budget");
   }
   if (ws && ws->n == n && ws->ncta == ncta && ws->tri >= (int)tri) return BC_OK;

@@ -125,6 +125,20 @@ void exec_release(Ctx *c, GraphExec *e) {
   if (e->d_reqbc) c->mem.release(e->d_reqbc, kReqPtrs * sizeof(double *));
 }
 
+// Frees a graph's cached workspaces (it has no request running); they are rebuilt on its next
+// request.
+void exec_trim(Ctx *c, GraphExec *e) {
+  exec_release(c, e);
+  e->ws = nullptr;
+  e->cta = nullptr;
+  e->d_many = nullptr;
+  e->cap_many = 0;
+  e->d_src = nullptr;
+  e->d_lane = nullptr;
+  e->d_reqbc = nullptr;
+  e->counted = false;
+}
+
 void finish(Server *sv, Req *r, bc_status st) {
   Ctx *c = sv->ctx;
   if (st == BC_OK && !r->canceled && r->d_bc && !r->src.empty()) {
@@ -153,14 +167,27 @@ void admit(Server *sv) {
     auto it = sv->gx.find(r->g);
     const bool ws_counted = it != sv->gx.end() && it->second->counted;
     if (!ws_counted) need += tile_ws_estimate(r->g, tile_width_for(r->g));
-    const bool fits = c->mem.budget == 0 || c->mem.used.load() + need <= c->mem.budget;
+    bool fits = c->mem.budget == 0 || c->mem.used.load() + need <= c->mem.budget;
     if (!fits && !sv->active.empty()) return;  // wait for memory to free up
-    sv->pending.pop_front();
+    if (!fits) {  // nothing runs: the cached workspaces of idle graphs give their memory back
+      for (auto &kv : sv->gx)
+        if (!kv.second->busy) exec_trim(c, kv.second);
+      need = (size_t)r->g->g.n * 8 + tile_ws_estimate(r->g, tile_width_for(r->g));
+      fits = c->mem.used.load() + need <= c->mem.budget;
+    }
     if (!fits) {
+      sv->pending.pop_front();
       finish(sv, r, fail(BC_ENOMEM, "serving: request does not fit the context HBM budget"));
       continue;
     }
     bc_status s = c->mem.alloc((void **)&r->d_bc, (size_t)r->g->g.n * 8);
+    if (s == BC_ENOMEM && c->mem.budget) {  // a worker's workspace took the room meanwhile
+      if (!sv->active.empty()) return;       // wait for memory to free up
+      for (auto &kv : sv->gx)
+        if (!kv.second->busy) exec_trim(c, kv.second);
+      s = c->mem.alloc((void **)&r->d_bc, (size_t)r->g->g.n * 8);
+    }
+    sv->pending.pop_front();
     // zeroed before a worker's stream (non-blocking, so unordered with this one) adds to it
     if (!s && (cudaMemsetAsync(r->d_bc, 0, (size_t)r->g->g.n * 8, nullptr) != cudaSuccess ||
                cudaStreamSynchronize(nullptr) != cudaSuccess))
