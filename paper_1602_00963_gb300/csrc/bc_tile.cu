@@ -96,7 +96,7 @@ struct TileCtl {
   int ovf_any;                  // some sigma of this tile passed 2^64
   unsigned ovf_lanes[8];        // lanes (sources) with an overflowed sigma
   // launched / graph mode registers
-  int level, mode, done, lmax, dlevel;
+  int level, mode, pmode, done, lmax, dlevel;  // pmode: the previous level's direction
   int a_pp, a_lo, a_hi, ecnt;
   long long levels;
   int trace_n;
@@ -1421,10 +1421,48 @@ __device__ void phase_mark(const TK &p, int level, int a0, int a1, int E1, int g
   }
 }
 
+// Bottom-up level following another bottom-up level: the non-hub vertices that some source
+// has not reached yet (of the per-graph list Lbu), appended to C with their degree prefix,
+// so that the pull walks only them (late bottom-up levels: most vertices are reached by
+// every source, and their edges would be walked for nothing).
+template <int G>
+__device__ void phase_compact(const TK &p, int level, int gwarp, int nwarps) {
+  const int lane = lane_id();
+  unsigned long long *cp = &p.ctl->cpack[level % 3];
+  for (int b = gwarp * 32; b < p.nbu; b += nwarps * 32) {
+    const int i = b + lane;
+    bool keep = false;
+    int w = 0, rw = 0, dw = 0;
+    if (i < p.nbu) {
+      w = p.Lbu[i];
+      uint32_t vv[G];
+      keep = !load_vis<G>(p, w, vv);
+      if (keep) {
+        rw = p.RPbu[i];
+        dw = p.rp[w + 1] - rw;
+      }
+    }
+    const unsigned mk = __ballot_sync(BC_FULL, keep);
+    if (!mk) continue;
+    int tot;
+    const int pre = warp_excl_scan(keep ? dw : 0, &tot);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(cp, pack_qe(__popc(mk), (unsigned)tot));
+    base = __shfl_sync(BC_FULL, base, 0);
+    if (keep) {
+      const int pos = (int)(base >> 32) + __popc(mk & lanemask_lt());
+      p.C[pos] = w;
+      p.CPD[pos] = (int)(base & 0xffffffffull) + pre;
+      p.CRP[pos] = rw;
+    }
+  }
+}
+
 // Pull of level l: hubs (Ch, or every hub in bottom-up mode) by whole CTAs, then the walk
 // over C (top-down) or over every non-hub vertex (bottom-up).  Reached vertices go to A_l.
 template <int G, bool EXT>
-__device__ void phase_pull(const TK &p, int level, bool bu, int a_lo, int a_base, int gwarp, int nwarps) {
+__device__ void phase_pull(const TK &p, int level, bool bu, bool compacted, int a_lo, int a_base, int gwarp,
+                           int nwarps) {
   const int lane = lane_id();
   const bool leaf = p.leaf_term && p.omega;
   unsigned long long nsacc[G];
@@ -1439,8 +1477,18 @@ __device__ void phase_pull(const TK &p, int level, bool bu, int a_lo, int a_base
   AppendBuf ab;
   ab.v = 0;
   ab.n = 0;
-  if (bu) {
-    pull_walk<G, EXT>(p, level, p.Lbu, p.PDbu, p.RPbu, p.nbu, p.Ebu, gwarp, nwarps, ab, ap, a_base, leaf, nsacc);
+  if (bu) {  // every non-hub vertex, or those some source has not reached (phase_compact)
+    const int32_t *L = p.Lbu, *PD = p.PDbu, *RP = p.RPbu;
+    int nl = p.nbu, el = p.Ebu;
+    if (compacted) {
+      const unsigned long long cpk = vload64(&p.ctl->cpack[level % 3]);
+      L = p.C;
+      PD = p.CPD;
+      RP = p.CRP;
+      nl = (int)(cpk >> 32);
+      el = (int)(cpk & 0xffffffffull);
+    }
+    pull_walk<G, EXT>(p, level, L, PD, RP, nl, el, gwarp, nwarps, ab, ap, a_base, leaf, nsacc);
   } else {
     const unsigned long long cpk = vload64(&p.ctl->cpack[level % 3]);
     const int nc = (int)(cpk >> 32);
@@ -2158,13 +2206,18 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) tile_persistent(TK p, int fw
   }
   bool bu = false;
   while (a_hi > a_lo) {
+    const bool pbu = bu;
     bu = next_dir(p, bu, ecnt);
+    const bool compact = bu && pbu;  // a second bottom-up level in a row
     phase_keep<G>(p, level, a_pp, a_lo, a_hi, gtid, nthr);
     if (!bu) {
       phase_mark<G>(p, level, a_lo, a_hi, ecnt, gwarp, nwarps);
       if (!tsync(p, gs, 1, level)) return;
+    } else if (compact) {
+      phase_compact<G>(p, level, gwarp, nwarps);
+      if (!tsync(p, gs, 1, level)) return;
     }
-    phase_pull<G, EXT>(p, level, bu, a_lo, a_hi, gwarp, nwarps);
+    phase_pull<G, EXT>(p, level, bu, compact, a_lo, a_hi, gwarp, nwarps);
     if (gtid == 0) {
       p.Lbits[level] = 0ull;  // A_level's sources are counted at the next level
       p.ctl->apack[(level + 1) % 3] = 0ull;
@@ -2236,6 +2289,7 @@ __global__ void k_init_src(TK p) {
   c->a_lo = 0;
   c->a_hi = (int)(pk >> 32);
   c->ecnt = (int)(pk & 0xffffffffull);
+  c->pmode = 0;
   c->mode = next_dir(p, false, c->ecnt);
   c->done = c->a_hi == 0;
   if (c->done) {
@@ -2250,7 +2304,10 @@ __global__ void __launch_bounds__(TPB<G>::value) k_fwd_mark(TK p) {
   if (c->done || c->bar.err) return;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   phase_keep<G>(p, c->level, c->a_pp, c->a_lo, c->a_hi, gtid, nthr);
-  if (!c->mode) phase_mark<G>(p, c->level, c->a_lo, c->a_hi, c->ecnt, warp_rank(), nthr >> 5);
+  if (!c->mode)
+    phase_mark<G>(p, c->level, c->a_lo, c->a_hi, c->ecnt, warp_rank(), nthr >> 5);
+  else if (c->pmode)
+    phase_compact<G>(p, c->level, warp_rank(), nthr >> 5);
 }
 
 template <int G, bool EXT>
@@ -2259,7 +2316,8 @@ __global__ void __launch_bounds__(TPB<G>::value, 1) k_fwd_pull(TK p) {
   if (c->done || c->bar.err) return;
   sparse_acc_clear<G>();
   const int nthr = gridDim.x * blockDim.x;
-  phase_pull<G, EXT>(p, c->level, c->mode != 0, c->a_lo, c->a_hi, warp_rank(), nthr >> 5);
+  phase_pull<G, EXT>(p, c->level, c->mode != 0, c->mode != 0 && c->pmode != 0, c->a_lo, c->a_hi, warp_rank(),
+                     nthr >> 5);
 }
 
 __global__ void k_fwd_end(TK p) {
@@ -2281,6 +2339,7 @@ __global__ void k_fwd_end(TK p) {
   c->level = level;
   p.Aoff[level] = c->a_hi;
   p.HEoff[level] = c->hecnt;
+  c->pmode = c->mode;
   c->mode = next_dir(p, c->mode != 0, c->ecnt);
   if ((long long)c->a_hi > p.capA) {  // appends past the active-list capacity were dropped
     atomicCAS(&c->bar.err, 0, BCD_CAPACITY);
