@@ -120,3 +120,16 @@ int main(void) {
     env = dict(os.environ, LD_LIBRARY_PATH=libdir + os.pathsep + os.environ.get("LD_LIBRARY_PATH", ""))
     r = subprocess.run([str(exe)], env=env, capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+
+
+def test_committed_traffic_matches_the_current_kernel():
+    """The ncu DRAM figure of the autotuner's tile width (T = 128 on the bench workload) was
+    taken on the current kernel code, so the bench reports it; other widths and stale code
+    give None."""
+    import json
+    import bench
+    path = os.path.join(ROOT, "profiles", "tile_rmat20_dram_T128.json")
+    j = json.load(open(path))
+    assert j["tile_width"] == 128
+    assert bench.ncu_traffic(128, 0.0) == float(j["dram_bytes_per_launch"])
+    assert bench.ncu_traffic(32, 0.0) is None
